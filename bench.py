@@ -1,0 +1,434 @@
+"""Benchmark: BF16 Stream-K GEMM shape sweep on GB300.
+
+One step = one pass of the hot path over the five BF16 sweep problems
+(3840x4096x4096, 1536x1536x8192, 8192x8192x8192, 2048x7168x1024,
+128x8192x16384; BF16 inputs uniform[-1,1], FP32 accumulate, BF16 output),
+each GEMM launched once in the library's default (Stream-K hybrid) mode.
+Inputs are resident in HBM; L2 is flushed (256 MB write) before every GEMM
+and only the GEMMs are inside the CUDA-event pairs.  The data-parallel
+tiling baseline (same kernel, one whole tile per CTA per wave) is timed the
+same way and reported beside it.
+
+Prints ONE JSON line (rank 0).  Under torchrun every rank runs the full
+workload on its own GPU (independent replicas, no collective on the data
+path); value = total flops of all ranks / max over ranks of the time.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import torch  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "GEMM TFLOP/s and % of dense peak, Stream-K vs data-parallel tiling, same GB300"
+UNIT = "TFLOP/s"
+WORKLOAD = ("BF16 Stream-K GEMM sweep (M,N,K) = " +
+            " ".join(f"({m},{n},{k})" for m, n, k in workloads.BF16_SWEEP) +
+            "; A row-major, B column-major, uniform[-1,1] -> BF16, FP32 accumulate, BF16 output")
+L2_FLUSH_BYTES = 256 << 20
+DOMINANT_SHAPE = (8192, 8192, 8192)
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sk_tc_kernel_bf16_8192cube.md")
+
+
+# --------------------------------------------------------------------- util
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return {"bf16": float(p["bf16_tflops"]), "bf16_sustained": float(p["bf16_tflops_sustained"]),
+                "hbm": float(p["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
+
+
+def kernel_sources_digest() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_00044_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(f.encode())
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, or None when the kernel sources changed since the capture."""
+    try:
+        txt = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    mh = re.search(r"kernel_sources_digest:\s*([0-9a-f]+)", txt)
+    mt = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    if not mh or not mt or mh.group(1) != kernel_sources_digest():
+        return None
+    return float(mt.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling in the background (200 ms)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        ident = str(gpu_index)
+        try:   # nvidia-smi ignores CUDA_VISIBLE_DEVICES: address the GPU by UUID
+            uuid = str(torch.cuda.get_device_properties(gpu_index).uuid)
+            ident = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            pass
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={ident}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(work: float, seconds: float, world: int):
+    """(total work over ranks, max time over ranks)."""
+    if world <= 1:
+        return work, seconds
+    import torch.distributed as dist
+    dev = torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([work, seconds], dtype=torch.float64, device=dev)
+    w = t[:1].clone()
+    s = t[1:].clone()
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(w.item()), float(s.item())
+
+
+# ------------------------------------------------------------ our GPU arm
+def run_ours(args, world, rank, local):
+    import paper_2407_00044_gb300 as sk
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pk = peaks()
+    shapes = list(workloads.BF16_SWEEP)
+    if args.only:
+        shapes = [tuple(int(x) for x in args.only.split(","))]
+    data = []
+    for i, (M, N, K) in enumerate(shapes):
+        a = workloads.device_uniform((M, K), seed=1000 + 2 * i, device=dev)
+        b = workloads.device_uniform((N, K), seed=1001 + 2 * i, device=dev).t()   # column-major
+        c = torch.empty(M, N, dtype=torch.bfloat16, device=dev)
+        data.append((a, b, c))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ws = sk.default_workspace(dev)
+    stream = torch.cuda.current_stream()
+
+    def one_pass(cfg, evs=None):
+        for i, (a, b, c) in enumerate(data):
+            flush.fill_(float(i))
+            if evs is not None:
+                evs[i][0].record(stream)
+            sk.gemm(a, b, c, config=cfg, workspace=ws)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    def timed(cfg, steps):
+        evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in shapes] for _ in range(steps)]
+        for s in range(steps):
+            one_pass(cfg, evs[s])
+        torch.cuda.synchronize()
+        per_shape = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(steps)] for i in range(len(shapes))]
+        return per_shape
+
+    auto = sk.Config(mode=args.mode)
+    dp = sk.Config(mode="dp")
+    for _ in range(args.warmup):
+        one_pass(auto)
+        if args.dp:
+            one_pass(dp)
+    torch.cuda.synchronize()
+    if ws.status() != 0:
+        raise RuntimeError("device status after warm-up")
+
+    # ---- timed region: Stream-K (default) arm
+    clocks = ClockSampler(local) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sk_ms = timed(auto, args.steps)
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop() if clocks else None
+    # ---- data-parallel baseline, same protocol
+    dp_ms = timed(dp, args.steps) if args.dp else sk_ms
+    if ws.status() != 0:
+        raise RuntimeError("device status after timing")
+
+    flops = [workloads.gemm_flops(*s) for s in shapes]
+    step_ms = sum(statistics.mean(v) for v in sk_ms)
+    total_flops_local = sum(flops) * args.steps
+    total_flops, max_s = aggregate(total_flops_local, step_ms * args.steps / 1e3, world)
+    value = total_flops / max_s / 1e12
+
+    per_shape = []
+    for (M, N, K), f, t_sk, t_dp in zip(shapes, flops, sk_ms, dp_ms):
+        ms_sk = statistics.median(t_sk)
+        ms_dp = statistics.median(t_dp)
+        per_shape.append({
+            "M": M, "N": N, "K": K,
+            "ms": round(ms_sk, 4), "tflops": round(f / ms_sk / 1e9, 1),
+            "pct_peak": round(100 * f / ms_sk / 1e9 / pk["bf16"], 1),
+            "dp_ms": round(ms_dp, 4), "dp_tflops": round(f / ms_dp / 1e9, 1),
+            "sk_over_dp": round(ms_dp / ms_sk, 3),
+        })
+    dp_step_ms = sum(statistics.mean(v) for v in dp_ms)
+
+    # roofline of the dominant launch (the 8192^3 GEMM)
+    di = shapes.index(DOMINANT_SHAPE) if DOMINANT_SHAPE in shapes else 0
+    dom_ms = statistics.mean(sk_ms[di])
+    achieved = flops[di] / (dom_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": round(achieved, 1), "peak": pk["bf16"], "unit": "TFLOP/s",
+                "frac": round(achieved / pk["bf16"], 4), "traffic": profiled_traffic(),
+                "kernel": "sk_tc_kernel<bf16,bf16,BN=256> on %dx%dx%d" % shapes[di],
+                "peak_source": f"{pk['source']} bf16 burst"}
+
+    # ---- end-to-end through the public API with host buffers
+    e2e = run_e2e(sk, shapes, data, args, ws, world) if args.e2e else None
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic: seeded uniform[-1,1] rounded to BF16 (torch CUDA generator)",
+        "config": {"workload": WORKLOAD, "mode": "library default (two-tile Stream-K + DP hybrid)",
+                   "tile": "128x256x64, 4-stage TMA ring, 2 TMEM accumulators",
+                   "l2": "flushed by a 256 MB write before every GEMM (outside the timed events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "dp_baseline": {"value": round(sum(flops) / (dp_step_ms / 1e3) / 1e12, 2), "unit": UNIT,
+                        "ms_per_step": round(dp_step_ms, 4)},
+        "shapes": per_shape,
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": len(shapes) * args.steps,
+        "clocks": clk,
+        "wall_s_timed_region": round(wall, 3),
+    }
+    if args.cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
+    return line
+
+
+def run_e2e(sk, shapes, data, args, ws, world):
+    """Same metric through the public API with pinned HOST buffers: every
+    step copies A and B host->device, runs the GEMM and copies C back."""
+    dev = data[0][0].device
+    host = []
+    h2d = d2h = 0
+    for (a, b, c) in data:
+        ha = torch.empty(a.shape, dtype=a.dtype, pin_memory=True).copy_(a)
+        hbt = torch.empty(b.t().shape, dtype=b.dtype, pin_memory=True).copy_(b.t())
+        hc = torch.empty(c.shape, dtype=c.dtype, pin_memory=True)
+        host.append((ha, hbt, hc))
+        h2d += ha.numel() * ha.element_size() + hbt.numel() * hbt.element_size()
+        d2h += hc.numel() * hc.element_size()
+    bufs = [(torch.empty_like(a), torch.empty_like(b.t()), torch.empty_like(c)) for (a, b, c) in data]
+    stream = torch.cuda.current_stream()
+    steps = max(1, min(args.steps, 5))
+
+    def step():
+        for (ha, hbt, hc), (da, dbt, dc) in zip(host, bufs):
+            da.copy_(ha, non_blocking=True)
+            dbt.copy_(hbt, non_blocking=True)
+            sk.gemm(da, dbt.t(), dc, workspace=ws)
+            hc.copy_(dc, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    flops = sum(workloads.gemm_flops(*s) for s in shapes)
+    tot, mx = aggregate(flops * steps, ms * steps / 1e3, world)
+    return {"value": round(tot / mx / 1e12, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3)}
+
+
+# -------------------------------------------------------- CPU oracle arm
+def cpu_baseline(seconds: float = 12.0):
+    """Time the FP64 oracle (as it stands) on a bounded sample of the sweep:
+    the first R rows of every sweep problem with full N and K, R chosen from
+    a short calibration so the whole sample takes about ``seconds``."""
+    import numpy as np
+
+    import oracle
+    threads = oracle.max_threads()
+    rng_seed = 7
+
+    def operands(R, N, K, seed):
+        # A row-major, B column-major (K contiguous), as in the GPU workload
+        a = workloads.uniform((R, K), seed=seed).to(torch.bfloat16)
+        b = workloads.uniform((N, K), seed=seed + 1).to(torch.bfloat16)
+        return oracle.to_f64(a), oracle.to_f64(b).T
+
+    # calibration: one row per thread of the first problem
+    M, N, K = workloads.BF16_SWEEP[0]
+    a64, b64 = operands(threads, N, K, rng_seed)
+    t0 = time.perf_counter()
+    oracle.gemm(a64, b64, threads=threads)
+    rate = workloads.gemm_flops(threads, N, K) / max(1e-6, time.perf_counter() - t0)
+    budget = rate * seconds / len(workloads.BF16_SWEEP)
+    done_flops = 0
+    t_total = 0.0
+    rows_used = []
+    for i, (M, N, K) in enumerate(workloads.BF16_SWEEP):
+        # whole multiples of the thread count, so every thread has rows
+        R = int(budget // (2 * N * K)) // threads * threads
+        R = int(max(threads, min(M, R)))
+        a64, b64 = operands(R, N, K, rng_seed + 10 * i)
+        t0 = time.perf_counter()
+        oracle.gemm(a64, b64, threads=threads)
+        t_total += time.perf_counter() - t0
+        done_flops += workloads.gemm_flops(R, N, K)
+        rows_used.append(R)
+    return {"value": round(done_flops / t_total / 1e12, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "first R rows (full N, K) of each sweep problem, R = " + ",".join(map(str, rows_used)) +
+                      f"; FP64 triple loop with |A||B| scale; {round(t_total, 1)} s",
+            "seconds": round(t_total, 2)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    per_step = max(1.0, args.ref_step_seconds)
+    # warm-up steps (untimed), then timed steps, each a bounded oracle sample
+    for _ in range(args.warmup):
+        cpu_baseline(seconds=min(per_step, 1.0))
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(seconds=per_step)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(wall / max(1, args.steps) * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded uniform[-1,1] rounded to BF16 (numpy Philox)",
+        "config": {"workload": WORKLOAD, "sample": last["sample"]},
+        "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+                         "sample": last["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-step-seconds", type=float, default=3.0)
+    ap.add_argument("--only", default="", help="M,N,K: time this one problem instead of the sweep")
+    ap.add_argument("--mode", default="auto", choices=["auto", "dp", "sk", "hybrid1", "hybrid2"])
+    ap.add_argument("--no-dp", dest="dp", action="store_false", help="skip the data-parallel baseline")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer run")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        if world > 1 or rank != 0:
+            args.cpu_baseline = args.cpu_baseline and rank == 0 and world == 1
+        line = run_ours(args, world, rank, local)
+    if line is not None and rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * skgemm -- Stream-K GEMM for NVIDIA GB300 (sm_103a), C ABI.
+ *
+ * Operation (paper, Introduction and Background: general matrix-matrix
+ * multiplication decomposed across GPU cores):
+ *
+ *     C = alpha * A * B + beta * C_in          A: m x k, B: k x n, C: m x n
+ *
+ * The MAC-loop iterations of all output tiles are split across one
+ * persistent CTA per SM ("Stream-K", the work-centric decomposition the
+ * paper studies; Introduction, Background, Methodology, after Osama et al.,
+ * PPoPP 2023).  Tiles that are cut between CTAs spill FP32 partials to a
+ * caller-provided workspace; the CTA that holds the tile's first k-block
+ * (its owner) waits on per-CTA flags and adds the partials in ascending CTA
+ * order, so the result is bit-reproducible for a fixed problem, config and
+ * CTA count.  A hybrid mode computes whole tiles in data-parallel waves
+ * (Background, Fig. 1) and only the ragged remainder Stream-K.  Ragged
+ * M, N and K are handled without padding (Results: the padding study).
+ *
+ * Conventions for every entry point:
+ *  - All pointers to matrices, scales and workspace are DEVICE pointers of
+ *    the current device; problem/config structs are HOST memory, read only
+ *    during the call.  The library never allocates device memory and keeps
+ *    no pointer after returning.
+ *  - Launches are asynchronous on `stream` (NULL = legacy default stream);
+ *    nothing synchronises the host except sk_get_status.
+ *  - Host-detectable errors return before anything is launched.  A device
+ *    side error (a bounded fixup wait that expired) is recorded in the
+ *    workspace's status word and read back with sk_get_status; the output
+ *    is then undefined.
+ *  - The first call on a device resolves device attributes and the driver's
+ *    tensor-map encoder; make it before capturing a stream into a CUDA graph.
+ */
+#ifndef SKGEMM_H
+#define SKGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SK_API __attribute__((visibility("default")))
+#else
+#define SK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, declared here so no CUDA header is needed. */
+typedef struct CUstream_st *sk_stream_t;
+
+typedef enum {
+    SK_OK = 0,
+    SK_ERR_INVALID_ARG = 1,         /* null pointer, negative size, bad enum, ld too small */
+    SK_ERR_UNSUPPORTED = 2,         /* valid but not implemented (dtype combo, alignment) */
+    SK_ERR_WORKSPACE_TOO_SMALL = 3, /* ws_bytes < sk_workspace_size() */
+    SK_ERR_TIMEOUT = 4,             /* a bounded device wait expired (from sk_get_status) */
+    SK_ERR_CUDA = 5,                /* a CUDA runtime/driver call failed */
+    SK_ERR_NO_DEVICE = 6            /* no CUDA device / architecture not sm_103 */
+} sk_status;
+
+typedef enum { SK_F32 = 0, SK_BF16 = 1, SK_E4M3 = 2 } sk_dtype;
+typedef enum { SK_ROW_MAJOR = 0, SK_COL_MAJOR = 1 } sk_layout;
+
+/* Work decomposition (paper, Background and Future Work; Osama et al.).
+ *  DP      : one whole output tile per CTA per wave.
+ *  SK      : all MAC-loop iterations of all tiles split evenly over the CTAs.
+ *  HYBRID1 : (tiles mod CTAs) tiles Stream-K, the rest in whole DP waves.
+ *  HYBRID2 : (CTAs + tiles mod CTAs) tiles Stream-K ("two-tile" Stream-K),
+ *            the rest in whole DP waves; all Stream-K when tiles <= CTAs.
+ *  AUTO    : the library's choice (currently HYBRID2).                    */
+typedef enum {
+    SK_MODE_AUTO = 0,
+    SK_MODE_DP = 1,
+    SK_MODE_SK = 2,
+    SK_MODE_HYBRID1 = 3,
+    SK_MODE_HYBRID2 = 4
+} sk_mode;
+
+/* One GEMM.  Element (i, j) of a row-major matrix X with leading dimension
+ * ldx lives at X[i * ldx + j]; of a column-major one at X[i + j * ldx].
+ * ld must be >= the contiguous extent.
+ * Supported type combinations:
+ *   A,B F32  -> C F32               (SIMT FFMA kernel, any layouts)
+ *   A,B BF16 -> C BF16 or F32       (tcgen05 kernel; FP32 accumulate)
+ *   A,B E4M3 -> C BF16 or F32       (tcgen05 kernel; FP32 accumulate;
+ *                                    A row-major and B column-major only)
+ * For BF16/E4M3 the TMA engine needs every base address 16-byte aligned and
+ * lda/ldb times the element size a multiple of 16 bytes (else UNSUPPORTED).
+ * C_in may equal C; it is read only when beta != 0 and must then have C's
+ * type, layout and ldc.  scale_a / scale_b (E4M3 only; NULL means 1.0) are
+ * device pointers to one float each, multiplied into alpha on the device. */
+typedef struct {
+    int64_t m, n, k;
+    sk_dtype a_type, b_type, c_type;
+    sk_layout a_layout, b_layout, c_layout;
+    int64_t lda, ldb, ldc;
+    const void *A;
+    const void *B;
+    const void *C_in;
+    void *C;
+    float alpha, beta;
+    const float *scale_a;
+    const float *scale_b;
+} sk_problem;
+
+/* Launch configuration.  Zero in any field selects the default. */
+typedef struct {
+    int tile_m;              /* 128 (all kernels) */
+    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (default 256) */
+    int stages;              /* smem pipeline depth (BF16/E4M3: 2..6; default by tile) */
+    sk_mode mode;            /* decomposition; default AUTO */
+    int num_ctas;            /* persistent CTAs g, 1 <= g <= SM count; 0 = SM count */
+    int min_iters_per_unit;  /* fewest k-blocks per Stream-K unit; default 4 */
+    uint64_t timeout_ns;     /* bound on every device-side wait; default 2e9 ns */
+    int debug_flags;         /* test-only fault injection, 0 in normal use:
+                                bit 0 = peers never raise their flags, so every
+                                owner's bounded wait expires (SK_ERR_TIMEOUT) */
+} sk_config;
+
+/* Resolved plan of a call, for inspection and tests. */
+typedef struct {
+    int tile_m, tile_n, tile_k, stages;
+    sk_mode mode;            /* never AUTO */
+    int num_ctas;            /* g */
+    int sk_units;            /* CTAs that take Stream-K iterations */
+    int64_t tiles;           /* output tiles over all problems */
+    int64_t sk_tiles;        /* leading tiles computed Stream-K */
+    int64_t dp_tiles;        /* tiles computed whole, round-robin */
+    int64_t sk_iters;        /* k-block iterations of the Stream-K tiles */
+    int64_t iters_per_unit;  /* floor(sk_iters / sk_units) */
+    int64_t extra_units;     /* sk_iters mod sk_units: units with one more */
+    size_t workspace_bytes;
+} sk_plan_info;
+
+/* One unit of work of one CTA, in the order that CTA processes it. */
+typedef enum { SK_ROLE_WHOLE = 0, SK_ROLE_OWNER = 1, SK_ROLE_PEER = 2, SK_ROLE_DP = 3 } sk_role;
+typedef struct {
+    int32_t problem;         /* index into the problem array */
+    int32_t tile;            /* tile index within the problem, before rasterisation */
+    int32_t tile_row, tile_col;   /* tile coordinates (rows of tile_m, cols of tile_n) */
+    int32_t k0, k1;          /* k-block range [k0, k1) */
+    int32_t role;            /* sk_role */
+    int32_t peer_first;      /* OWNER: peers are CTAs peer_first..peer_last, */
+    int32_t peer_last;       /*        added in this ascending order          */
+    int32_t pad;
+    int64_t global_tile;     /* tile index over the concatenated problems */
+} sk_work_item;
+
+/* Bytes of workspace a call with these problems and config needs
+ * (per-CTA partial slots, per-CTA flags, one status word).  `count` >= 1.
+ * If cfg->num_ctas is 0 the current device's SM count is used (needs a
+ * device).  Host-only; no launch. */
+SK_API sk_status sk_workspace_size(const sk_problem *problems, int count,
+                            const sk_config *cfg, size_t *bytes);
+
+/* Zero a workspace (flags and status word must start at zero).  Needed once
+ * after allocation and after any call that reported SK_ERR_TIMEOUT; a
+ * completed call leaves every flag it used back at zero. */
+SK_API sk_status sk_workspace_init(void *ws, size_t ws_bytes, sk_stream_t stream);
+
+/* C = alpha*A*B + beta*C_in for one problem.  ws must hold
+ * sk_workspace_size() bytes, be 256-byte aligned, and not be used by
+ * another call that may run concurrently on the GPU. */
+SK_API sk_status sk_gemm(const sk_problem *problem, const sk_config *cfg,
+                  void *ws, size_t ws_bytes, sk_stream_t stream);
+
+/* `count` independent GEMMs (1 <= count <= 64) in ONE persistent launch.
+ * The problems' tiles are concatenated and the decomposition runs over all
+ * of them, so Stream-K ranges cross problem boundaries.  All problems must
+ * share a_type, b_type and c_type.  Outputs must not overlap. */
+SK_API sk_status sk_gemm_grouped(const sk_problem *problems, int count,
+                          const sk_config *cfg, void *ws, size_t ws_bytes,
+                          sk_stream_t stream);
+
+/* Backward of C = A*B (alpha = 1 semantics): given dC (m x n, row-major,
+ * leading dimension lddc, type fwd->c_type), compute
+ *     dA = dC * B^T   (m x k, same type/layout as A, leading dimension ldda)
+ *     dB = A^T * dC   (k x n, same type/layout as B, leading dimension lddb)
+ * in one grouped launch of two Stream-K GEMMs whose operands are read in
+ * transposed order directly (no transposed copies).  Either of dA, dB may
+ * be NULL to skip it.  BF16 only. */
+SK_API sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc,
+                           void *dA, int64_t ldda, void *dB, int64_t lddb,
+                           const sk_config *cfg, void *ws, size_t ws_bytes,
+                           sk_stream_t stream);
+
+/* Per-tensor FP8 quantisation: scale = amax(|x|)/448 (1 if x == 0),
+ * q = E4M3(x / scale) rounded to nearest even and saturated to +-448.
+ * x: n float32 values; q: n bytes; scale_out: one float; amax_work: one
+ * float of scratch.  All device pointers. */
+SK_API sk_status sk_quantize_e4m3(const float *x, int64_t n, uint8_t *q,
+                           float *scale_out, float *amax_work,
+                           sk_stream_t stream);
+
+/* Synchronise `stream`, read the workspace's status word (SK_OK or
+ * SK_ERR_TIMEOUT) into *device_status, and clear it if `clear`. */
+SK_API sk_status sk_get_status(const void *ws, size_t ws_bytes, sk_stream_t stream,
+                        int clear, sk_status *device_status);
+
+/* Human-readable name of a status code (static string). */
+SK_API const char *sk_status_string(sk_status s);
+
+/* Resolve a call's plan without launching anything.  num_sms > 0 overrides
+ * the device's SM count (then no device is needed). */
+SK_API sk_status sk_plan_query(const sk_problem *problems, int count,
+                        const sk_config *cfg, int num_sms, sk_plan_info *out);
+
+/* The work items CTA `unit` of that plan processes, in order, computed by
+ * the same scheduler code the kernels run.  Writes at most `max_items`
+ * items and the total count to *n_items. */
+SK_API sk_status sk_plan_unit_items(const sk_problem *problems, int count,
+                             const sk_config *cfg, int num_sms, int unit,
+                             sk_work_item *items, int max_items, int *n_items);
+
+/* Library version string. */
+SK_API const char *sk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SKGEMM_H */

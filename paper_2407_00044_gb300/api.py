@@ -1,0 +1,268 @@
+"""Torch-tensor front end of the C ABI: reads shapes, strides, dtypes and
+device pointers off tensors, owns a per-device workspace, and calls the
+library on the current CUDA stream.  No arithmetic happens here.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+from dataclasses import dataclass
+
+import torch
+
+from . import binding as B
+
+_DTYPES = {torch.float32: B.SK_F32, torch.bfloat16: B.SK_BF16,
+           torch.float8_e4m3fn: B.SK_E4M3, torch.uint8: B.SK_E4M3}
+_OUT_TORCH = {B.SK_F32: torch.float32, B.SK_BF16: torch.bfloat16}
+
+
+@dataclass
+class Config:
+    """Python mirror of ``sk_config`` (0 / 'auto' = library default)."""
+    tile_m: int = 0
+    tile_n: int = 0
+    stages: int = 0
+    mode: str = "auto"
+    num_ctas: int = 0
+    min_iters_per_unit: int = 0
+    timeout_ns: int = 0
+    debug_flags: int = 0
+
+    def to_c(self) -> B.sk_config:
+        c = B.sk_config()
+        c.tile_m = self.tile_m
+        c.tile_n = self.tile_n
+        c.stages = self.stages
+        c.mode = B.MODE_NAMES[self.mode] if isinstance(self.mode, str) else int(self.mode)
+        c.num_ctas = self.num_ctas
+        c.min_iters_per_unit = self.min_iters_per_unit
+        c.timeout_ns = self.timeout_ns
+        c.debug_flags = self.debug_flags
+        return c
+
+
+def _cfg(config) -> B.sk_config:
+    if config is None:
+        return Config().to_c()
+    if isinstance(config, B.sk_config):
+        return config
+    if isinstance(config, dict):
+        return Config(**config).to_c()
+    return config.to_c()
+
+
+def layout_of(t: torch.Tensor):
+    """(sk_layout, leading dimension) of a 2-D tensor, from its strides."""
+    if t.dim() != 2:
+        raise ValueError("expected a 2-D tensor")
+    r, c = t.shape
+    if t.numel() == 0:
+        return B.SK_ROW_MAJOR, max(1, c)
+    s0, s1 = t.stride()
+    if s1 == 1 and (r <= 1 or s0 >= max(1, c)):
+        ld = s0 if r > 1 else -(-max(1, c) // 16) * 16
+        return B.SK_ROW_MAJOR, ld
+    if s0 == 1 and (c <= 1 or s1 >= max(1, r)):
+        ld = s1 if c > 1 else -(-max(1, r) // 16) * 16
+        return B.SK_COL_MAJOR, ld
+    raise ValueError(f"tensor with strides {t.stride()} is neither row- nor column-major")
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def make_problem(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor, *, C_in=None,
+                 alpha: float = 1.0, beta: float = 0.0, scale_a=None, scale_b=None) -> B.sk_problem:
+    M, K = A.shape
+    K2, N = Bm.shape
+    if K != K2 or tuple(C.shape) != (M, N):
+        raise ValueError(f"shape mismatch A{tuple(A.shape)} B{tuple(Bm.shape)} C{tuple(C.shape)}")
+    p = B.sk_problem()
+    p.m, p.n, p.k = M, N, K
+    p.a_type = _DTYPES[A.dtype]
+    p.b_type = _DTYPES[Bm.dtype]
+    p.c_type = _DTYPES[C.dtype]
+    p.a_layout, p.lda = layout_of(A)
+    p.b_layout, p.ldb = layout_of(Bm)
+    p.c_layout, p.ldc = layout_of(C)
+    p.A = A.data_ptr()
+    p.B = Bm.data_ptr()
+    p.C = C.data_ptr()
+    p.C_in = C_in.data_ptr() if C_in is not None else None
+    if C_in is not None and (C_in.dtype != C.dtype or C_in.stride() != C.stride()):
+        raise ValueError("C_in must have C's dtype and strides")
+    p.alpha = float(alpha)
+    p.beta = float(beta)
+    p.scale_a = scale_a.data_ptr() if scale_a is not None else None
+    p.scale_b = scale_b.data_ptr() if scale_b is not None else None
+    return p
+
+
+class Workspace:
+    """A zero-initialised device buffer large enough for any call on one
+    device (sized for the largest tile and every SM)."""
+
+    def __init__(self, device=None, nbytes: int | None = None):
+        self.device = torch.device(device if device is not None else torch.cuda.current_device())
+        if nbytes is None:
+            sms = torch.cuda.get_device_properties(self.device).multi_processor_count
+            nbytes = 256 + (-(-sms * 4 // 256)) * 256 + sms * 128 * 256 * 4
+        self.nbytes = int(nbytes)
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
+        with torch.cuda.device(self.device):
+            B.check(B.sk_workspace_init(ctypes.c_void_p(self.buf.data_ptr()), self.nbytes,
+                                        _stream()), "sk_workspace_init")
+
+    @property
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+    def status(self, clear: bool = True) -> int:
+        out = ctypes.c_int(0)
+        with torch.cuda.device(self.device):
+            B.check(B.sk_get_status(self.ptr, self.nbytes, _stream(), int(clear), ctypes.byref(out)),
+                    "sk_get_status")
+        return out.value
+
+
+_ws_lock = threading.Lock()
+_ws_cache: dict = {}
+
+
+def default_workspace(device=None) -> Workspace:
+    dev = torch.device(device if device is not None else torch.cuda.current_device())
+    if dev.index is None:
+        dev = torch.device("cuda", torch.cuda.current_device())
+    with _ws_lock:
+        ws = _ws_cache.get(dev.index)
+        if ws is None:
+            ws = Workspace(dev)
+            _ws_cache[dev.index] = ws
+        return ws
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def gemm(A: torch.Tensor, Bm: torch.Tensor, out: torch.Tensor | None = None, *,
+         alpha: float = 1.0, beta: float = 0.0, C_in: torch.Tensor | None = None,
+         out_dtype=None, scale_a=None, scale_b=None, config=None,
+         workspace: Workspace | None = None) -> torch.Tensor:
+    """C = alpha * A @ B + beta * C_in on the current stream (Stream-K)."""
+    if out is None:
+        dt = out_dtype or (torch.float32 if A.dtype == torch.float32 else torch.bfloat16)
+        out = torch.empty((A.shape[0], Bm.shape[1]), dtype=dt, device=A.device)
+    ws = workspace or default_workspace(A.device)
+    p = make_problem(A, Bm, out, C_in=C_in, alpha=alpha, beta=beta, scale_a=scale_a, scale_b=scale_b)
+    cfg = _cfg(config)
+    B.check(B.sk_gemm(ctypes.byref(p), ctypes.byref(cfg), ws.ptr, ws.nbytes, _stream()), "sk_gemm")
+    return out
+
+
+def grouped_gemm(As, Bs, outs=None, *, alpha: float = 1.0, beta: float = 0.0, C_ins=None,
+                 out_dtype=None, config=None, workspace: Workspace | None = None):
+    """One persistent launch over len(As) independent GEMMs."""
+    n = len(As)
+    if outs is None:
+        outs = [torch.empty((a.shape[0], b.shape[1]),
+                            dtype=out_dtype or (torch.float32 if a.dtype == torch.float32 else torch.bfloat16),
+                            device=a.device) for a, b in zip(As, Bs)]
+    arr = (B.sk_problem * n)()
+    for i in range(n):
+        arr[i] = make_problem(As[i], Bs[i], outs[i], C_in=None if C_ins is None else C_ins[i],
+                              alpha=alpha, beta=beta)
+    ws = workspace or default_workspace(As[0].device)
+    cfg = _cfg(config)
+    B.check(B.sk_gemm_grouped(arr, n, ctypes.byref(cfg), ws.ptr, ws.nbytes, _stream()), "sk_gemm_grouped")
+    return outs
+
+
+def gemm_backward(A: torch.Tensor, Bm: torch.Tensor, dC: torch.Tensor, *, need_dA: bool = True,
+                  need_dB: bool = True, config=None, workspace: Workspace | None = None):
+    """dA = dC @ B^T and dB = A^T @ dC, with dA/dB in A's/B's dtype and
+    storage order, in one grouped Stream-K launch."""
+    M, K = A.shape
+    N = Bm.shape[1]
+    dA = torch.empty_strided(A.shape, A.stride(), dtype=A.dtype, device=A.device) if need_dA else None
+    dB = torch.empty_strided(Bm.shape, Bm.stride(), dtype=Bm.dtype, device=Bm.device) if need_dB else None
+    c_layout, lddc = layout_of(dC)
+    if c_layout != B.SK_ROW_MAJOR:
+        raise ValueError("dC must be row-major")
+    fwd = B.sk_problem()
+    fwd.m, fwd.n, fwd.k = M, N, K
+    fwd.a_type, fwd.b_type, fwd.c_type = _DTYPES[A.dtype], _DTYPES[Bm.dtype], _DTYPES[dC.dtype]
+    fwd.a_layout, fwd.lda = layout_of(A)
+    fwd.b_layout, fwd.ldb = layout_of(Bm)
+    fwd.c_layout, fwd.ldc = B.SK_ROW_MAJOR, lddc
+    fwd.A, fwd.B = A.data_ptr(), Bm.data_ptr()
+    fwd.alpha, fwd.beta = 1.0, 0.0
+    ldda = layout_of(dA)[1] if dA is not None else 0
+    lddb = layout_of(dB)[1] if dB is not None else 0
+    ws = workspace or default_workspace(A.device)
+    cfg = _cfg(config)
+    B.check(B.sk_gemm_backward(ctypes.byref(fwd), _ptr(dC), lddc, _ptr(dA), ldda, _ptr(dB), lddb,
+                               ctypes.byref(cfg), ws.ptr, ws.nbytes, _stream()), "sk_gemm_backward")
+    return dA, dB
+
+
+def quantize_e4m3(x: torch.Tensor):
+    """Per-tensor FP8 quantisation on the GPU: returns (codes uint8, scale)."""
+    x = x.contiguous()
+    if x.dtype != torch.float32:
+        raise ValueError("x must be float32")
+    q = torch.empty(x.shape, dtype=torch.uint8, device=x.device)
+    scale = torch.empty((), dtype=torch.float32, device=x.device)
+    amax = torch.empty((), dtype=torch.float32, device=x.device)
+    B.check(B.sk_quantize_e4m3(_ptr(x), x.numel(), _ptr(q), _ptr(scale), _ptr(amax), _stream()),
+            "sk_quantize_e4m3")
+    return q, scale
+
+
+def plan(problems, config=None, num_sms: int = 0):
+    """Resolve the plan of a call (no launch).  ``problems`` is an
+    ``sk_problem`` or a list of them."""
+    if isinstance(problems, B.sk_problem):
+        problems = [problems]
+    arr = (B.sk_problem * len(problems))(*problems)
+    info = B.sk_plan_info()
+    cfg = _cfg(config)
+    B.check(B.sk_plan_query(arr, len(problems), ctypes.byref(cfg), num_sms, ctypes.byref(info)),
+            "sk_plan_query")
+    return info
+
+
+def unit_items(problems, unit: int, config=None, num_sms: int = 0):
+    if isinstance(problems, B.sk_problem):
+        problems = [problems]
+    arr = (B.sk_problem * len(problems))(*problems)
+    cfg = _cfg(config)
+    n = ctypes.c_int(0)
+    B.check(B.sk_plan_unit_items(arr, len(problems), ctypes.byref(cfg), num_sms, unit, None, 0,
+                                 ctypes.byref(n)), "sk_plan_unit_items")
+    items = (B.sk_work_item * max(1, n.value))()
+    B.check(B.sk_plan_unit_items(arr, len(problems), ctypes.byref(cfg), num_sms, unit, items,
+                                 n.value, ctypes.byref(n)), "sk_plan_unit_items")
+    return [items[i] for i in range(n.value)]
+
+
+def shape_problem(M: int, N: int, K: int, dtype: str = "bf16", out: str | None = None,
+                  a_layout: str = "row", b_layout: str = "col") -> B.sk_problem:
+    """A pointer-free problem description for plan queries."""
+    t = {"f32": B.SK_F32, "bf16": B.SK_BF16, "e4m3": B.SK_E4M3}[dtype]
+    ct = {"f32": B.SK_F32, "bf16": B.SK_BF16}[out or ("f32" if dtype == "f32" else "bf16")]
+    p = B.sk_problem()
+    p.m, p.n, p.k = M, N, K
+    p.a_type = p.b_type = t
+    p.c_type = ct
+    p.a_layout = B.SK_ROW_MAJOR if a_layout == "row" else B.SK_COL_MAJOR
+    p.b_layout = B.SK_ROW_MAJOR if b_layout == "row" else B.SK_COL_MAJOR
+    p.c_layout = B.SK_ROW_MAJOR
+    p.lda = max(1, K if a_layout == "row" else M)
+    p.ldb = max(1, N if b_layout == "row" else K)
+    p.ldc = max(1, N)
+    p.A = p.B = p.C = 16   # non-null placeholders; plan queries never dereference
+    p.alpha, p.beta = 1.0, 0.0
+    return p

@@ -1,0 +1,93 @@
+// Small HBM-bound helper kernels: the k == 0 epilogue (C = beta * C_in) and
+// per-tensor FP8 E4M3 quantisation.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "common.cuh"
+
+namespace sk {
+
+namespace {
+
+template <typename T>
+__global__ void scale_kernel(T *C, const T *C_in, int64_t ldc, int64_t M, int64_t N, float beta) {
+  const int64_t total = M * N;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx / N, j = idx - (idx / N) * N;
+    float v = 0.f;
+    if (beta != 0.f) v = beta * static_cast<float>(C_in[i * ldc + j]);
+    C[i * ldc + j] = static_cast<T>(v);
+  }
+}
+
+// amax over |x| as the bit pattern of a non-negative float (monotone in the
+// value, so an unsigned atomicMax is exact).  NaNs are ignored.
+__global__ void amax_kernel(const float *x, int64_t n, unsigned int *amax_bits) {
+  float m = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf(x[i]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float wmax[32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) atomicMax(amax_bits, __float_as_uint(m));
+  }
+}
+
+// scale = amax / 448 (1 if amax == 0); q = E4M3(x / scale), round to nearest
+// even, saturating to +-448 (satfinite conversion).
+__global__ void quant_kernel(const float *x, int64_t n, uint8_t *q, float *scale_out, const float *amax) {
+  const float a = *amax;
+  const float s = a > 0.f ? __fdiv_rn(a, 448.0f) : 1.0f;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *scale_out = s;
+  const int64_t pairs = n / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < pairs; i += (int64_t)gridDim.x * blockDim.x) {
+    float2 v = reinterpret_cast<const float2 *>(x)[i];
+    v.x = __fdiv_rn(v.x, s);
+    v.y = __fdiv_rn(v.y, s);
+    __nv_fp8x2_storage_t r = __nv_cvt_float2_to_fp8x2(v, __NV_SATFINITE, __NV_E4M3);
+    reinterpret_cast<__nv_fp8x2_storage_t *>(q)[i] = r;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    q[n - 1] = __nv_cvt_float_to_fp8(__fdiv_rn(x[n - 1], s), __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N, float beta, int c_is_f32,
+                         cudaStream_t st) {
+  const int64_t total = M * N;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  if (c_is_f32)
+    scale_kernel<float><<<blocks, 256, 0, st>>>(static_cast<float *>(C), static_cast<const float *>(C_in), ldc, M, N,
+                                                beta);
+  else
+    scale_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<__nv_bfloat16 *>(C),
+                                                        static_cast<const __nv_bfloat16 *>(C_in), ldc, M, N, beta);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_quant_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_out, float *amax_work,
+                              cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(amax_work, 0, sizeof(float), st);
+  if (e != cudaSuccess) return e;
+  int blocks = (int)((n + 1023) / 1024);
+  if (blocks > 2048) blocks = 2048;
+  if (blocks < 1) blocks = 1;
+  amax_kernel<<<blocks, 256, 0, st>>>(x, n, reinterpret_cast<unsigned int *>(amax_work));
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  quant_kernel<<<blocks, 256, 0, st>>>(x, n, q, scale_out, amax_work);
+  return cudaGetLastError();
+}
+
+}  // namespace sk

@@ -1,0 +1,101 @@
+// Kernel parameter blocks and launch declarations shared by the C-ABI layer
+// and the kernel translation units.
+#pragma once
+#include <cuda.h>          // CUtensorMap (type only; the driver is reached at run time)
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sched.cuh"
+
+namespace sk {
+
+constexpr int MAXP_GROUPED = 64;      // problems per grouped launch
+constexpr uint32_t STATUS_TIMEOUT = 4;  // == SK_ERR_TIMEOUT
+
+// Device views of the caller's workspace.
+struct Workspace {
+  float *partials;      // g slots of tile_m * tile_n floats
+  uint32_t *flags;      // g flags, zero between calls
+  uint32_t *status;     // 0, or STATUS_TIMEOUT after an expired wait
+};
+
+// ----------------------------------------------------------- FP32 SIMT path
+constexpr int F32_BM = 128, F32_BN = 128, F32_BK = 16, F32_THREADS = 256;
+
+struct SimtProblem {
+  const float *A, *B, *C_in;
+  float *C;
+  int64_t a_rs, a_cs;   // A(i,k) = A[i*a_rs + k*a_cs]
+  int64_t b_rs, b_cs;   // B(k,j) = B[k*b_rs + j*b_cs]
+  int64_t ldc;          // C row-major (C_in shares it)
+  int32_t M, N, K;
+  float alpha, beta;
+  int32_t a_kmajor;     // a_cs == 1
+  int32_t b_kmajor;     // b_rs == 1
+  int32_t a_vec, b_vec, c_vec;   // 16-byte vector access legal
+};
+
+// debug_flags bit 0: peers do not raise their flags (test-only; makes every
+// owner's bounded wait expire).
+constexpr int32_t DEBUG_SKIP_PEER_FLAG = 1;
+
+template <int MAXP>
+struct SimtParams {
+  Sched sched;
+  ProbSched ps[MAXP];
+  SimtProblem prob[MAXP];
+  Workspace ws;
+  uint64_t timeout_ns;
+  int32_t debug_flags;
+};
+
+// --------------------------------------------------------- tcgen05 path
+enum InKind : int { IN_BF16 = 0, IN_E4M3 = 1 };
+
+struct TcProblem {
+  CUtensorMap tmap_a;   // K-major: box {BK, 128}; MN-major: box {64, BK}
+  CUtensorMap tmap_b;   // K-major: box {BK, BN};  MN-major: box {64, BK}
+  void *C;
+  const void *C_in;
+  int64_t ldc;          // C row-major
+  int32_t M, N, K;
+  float alpha, beta;
+  int32_t a_mn, b_mn;   // operand stored MN-major (transposed) in memory
+  int32_t c_vec;        // 16-byte vector stores legal for C / C_in
+  const float *scale_a, *scale_b;   // E4M3 per-tensor scales (may be null)
+};
+
+template <int MAXP>
+struct TcParams {
+  TcProblem prob[MAXP];
+  ProbSched ps[MAXP];
+  Sched sched;
+  Workspace ws;
+  uint64_t timeout_ns;
+  int32_t stages;
+  int32_t debug_flags;
+};
+
+// Bytes of dynamic shared memory of a tcgen05 launch.  Never less than
+// 120 KB, so two CTAs can never share an SM: each CTA holds up to all 512
+// TMEM columns, and an owner CTA waits on peer CTAs, so a peer stuck in
+// tcgen05.alloc behind its owner on the same SM would stall until timeout.
+inline int tc_smem_bytes(int bn, int stages) {
+  const int stage = 128 * 128 + bn * 128;
+  const int need = 1024 /*alignment slack*/ + stages * stage + 256 /*barriers, TMEM slot*/;
+  return need < 120 * 1024 ? 120 * 1024 : need;
+}
+
+template <int MAXP>
+cudaError_t launch_simt_f32(const SimtParams<MAXP> &p, int grid, cudaStream_t st);
+
+template <int IN, typename OutT, int BN, int MAXP>
+cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st);
+
+cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N,
+                         float beta, int c_is_f32, cudaStream_t st);
+
+cudaError_t launch_quant_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_out,
+                              float *amax_work, cudaStream_t st);
+
+}  // namespace sk

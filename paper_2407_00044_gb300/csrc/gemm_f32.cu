@@ -1,0 +1,243 @@
+// FP32 Stream-K GEMM on the SIMT FFMA pipes.
+//
+// One persistent CTA per unit walks the items the scheduler gives it
+// (Stream-K segments first, then data-parallel tiles).  For each item it
+// accumulates its k-block range of a 128x128 tile in registers (8x8 per
+// thread), then, by role:
+//   peer  : writes the FP32 partial to its workspace slot and raises its flag
+//   owner : waits for its peers' flags (bounded), adds their partials in
+//           ascending CTA order, then runs the epilogue
+//   whole / dp : runs the epilogue
+// Epilogue: C = alpha * acc + beta * C_in, bounds-masked (no padding).
+// FP32 needs FFMA: TF32 tensor-core products would miss the 5e-5 relative
+// accuracy this path promises.
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace sk {
+
+namespace {
+
+constexpr int PAD = 4;
+
+struct F32Smem {
+  float As[2][F32_BK][F32_BM + PAD];
+  float Bs[2][F32_BK][F32_BN + PAD];
+  uint32_t timed_out;
+};
+
+// Load the 128 x 16 slice of an operand into registers.  `rows` index the
+// output dimension (M for A, N for B), `ks` the reduction dimension.
+// kmajor: element (r, k) at X[r*rs + k] -> thread reads 8 consecutive k of one row.
+// else  : element (r, k) at X[r + k*cs] -> thread reads 8 consecutive rows of one k.
+__device__ __forceinline__ void load_slice(const float *X, int64_t rs, int64_t cs, int kmajor,
+                                           int vec, int R, int Kd, int r0, int k0, float (&v)[8]) {
+  const int t = threadIdx.x;
+  if (kmajor) {
+    const int r = r0 + (t & 127);
+    const int k = k0 + (t >> 7) * 8;
+    if (r < R) {
+      const float *p = X + (int64_t)r * rs + k;
+      if (vec && k + 8 <= Kd) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (k + e < Kd) ? __ldg(p + e) : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = 0.f;
+    }
+  } else {
+    const int k = k0 + (t >> 4);
+    const int r = r0 + (t & 15) * 8;
+    if (k < Kd) {
+      const float *p = X + (int64_t)k * cs + r;
+      if (vec && r + 8 <= R) {
+        float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+        float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (r + e < R) ? __ldg(p + e) : 0.f;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = 0.f;
+    }
+  }
+}
+
+__device__ __forceinline__ void store_slice(float (*S)[F32_BM + PAD], int kmajor, const float (&v)[8]) {
+  const int t = threadIdx.x;
+  if (kmajor) {
+    const int r = t & 127, k = (t >> 7) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) S[k + e][r] = v[e];
+  } else {
+    const int k = t >> 4, r = (t & 15) * 8;
+    *reinterpret_cast<float4 *>(&S[k][r]) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4 *>(&S[k][r + 4]) = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+template <int MAXP>
+__global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __grid_constant__ SimtParams<MAXP> P) {
+  __shared__ __align__(16) F32Smem sm;
+  const int t = threadIdx.x;
+  const int ty = t >> 4, tx = t & 15;
+  const int u = blockIdx.x;
+  const Sched &S = P.sched;
+
+  Cursor cur;
+  cursor_init(S, u, cur);
+  Item w;
+  while (cursor_next(S, P.ps, u, cur, w)) {
+    const SimtProblem &pr = P.prob[w.problem];
+    const int m0 = w.tm * F32_BM, n0 = w.tn * F32_BN;
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+
+    float ra[8], rb[8];
+    load_slice(pr.A, pr.a_rs, pr.a_cs, pr.a_kmajor, pr.a_vec, pr.M, pr.K, m0, w.k0 * F32_BK, ra);
+    load_slice(pr.B, pr.b_cs, pr.b_rs, pr.b_kmajor, pr.b_vec, pr.N, pr.K, n0, w.k0 * F32_BK, rb);
+    store_slice(sm.As[0], pr.a_kmajor, ra);
+    store_slice(sm.Bs[0], pr.b_kmajor, rb);
+    __syncthreads();
+
+    for (int kb = w.k0; kb < w.k1; ++kb) {
+      const int buf = (kb - w.k0) & 1;
+      const bool more = kb + 1 < w.k1;
+      if (more) {
+        load_slice(pr.A, pr.a_rs, pr.a_cs, pr.a_kmajor, pr.a_vec, pr.M, pr.K, m0, (kb + 1) * F32_BK, ra);
+        load_slice(pr.B, pr.b_cs, pr.b_rs, pr.b_kmajor, pr.b_vec, pr.N, pr.K, n0, (kb + 1) * F32_BK, rb);
+      }
+#pragma unroll
+      for (int kk = 0; kk < F32_BK; ++kk) {
+        float a[8], b[8];
+        float4 a0 = *reinterpret_cast<const float4 *>(&sm.As[buf][kk][ty * 4]);
+        float4 a1 = *reinterpret_cast<const float4 *>(&sm.As[buf][kk][64 + ty * 4]);
+        float4 b0 = *reinterpret_cast<const float4 *>(&sm.Bs[buf][kk][tx * 4]);
+        float4 b1 = *reinterpret_cast<const float4 *>(&sm.Bs[buf][kk][64 + tx * 4]);
+        a[0] = a0.x; a[1] = a0.y; a[2] = a0.z; a[3] = a0.w;
+        a[4] = a1.x; a[5] = a1.y; a[6] = a1.z; a[7] = a1.w;
+        b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+        b[4] = b1.x; b[5] = b1.y; b[6] = b1.z; b[7] = b1.w;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+      }
+      if (more) {
+        store_slice(sm.As[buf ^ 1], pr.a_kmajor, ra);
+        store_slice(sm.Bs[buf ^ 1], pr.b_kmajor, rb);
+      }
+      __syncthreads();
+    }
+
+    // Partial slot layout: float4 index v*256 + t, v = row_group*2 + col_half,
+    // so consecutive threads touch consecutive 16-byte words.
+    float4 *slot_base = reinterpret_cast<float4 *>(P.ws.partials);
+    const int64_t slot_f4 = (int64_t)F32_BM * F32_BN / 4;
+
+    if (w.role == ROLE_PEER) {
+      float4 *slot = slot_base + (int64_t)u * slot_f4;
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          __stcg(slot + (i * 2 + h) * F32_THREADS + t,
+                 make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]));
+      __threadfence();
+      __syncthreads();
+      if (t == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + u, 1u);
+      continue;
+    }
+
+    if (w.role == ROLE_OWNER) {
+      if (t == 0) {
+        sm.timed_out = 0;
+        const uint64_t t0 = globaltimer();
+        for (int p = w.peer_first; p <= w.peer_last && !sm.timed_out; ++p) {
+          while (ld_acquire_gpu(P.ws.flags + p) == 0u) {
+            if (globaltimer() - t0 > P.timeout_ns) {
+              atomicExch(P.ws.status, STATUS_TIMEOUT);
+              sm.timed_out = 1;
+              break;
+            }
+          }
+        }
+      }
+      __syncthreads();
+      // Fixed summation order: own partial, then peers in ascending CTA index.
+      for (int p = w.peer_first; p <= w.peer_last; ++p) {
+        const float4 *slot = slot_base + (int64_t)p * slot_f4;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            float4 v = __ldcg(slot + (i * 2 + h) * F32_THREADS + t);
+            acc[i][h * 4 + 0] += v.x;
+            acc[i][h * 4 + 1] += v.y;
+            acc[i][h * 4 + 2] += v.z;
+            acc[i][h * 4 + 3] += v.w;
+          }
+      }
+      __syncthreads();
+      if (t == 0)
+        for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[p] = 0u;
+    }
+
+    // Epilogue.
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int row = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+      if (row >= pr.M) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int col = n0 + h * 64 + tx * 4;
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o[e] = pr.alpha * acc[i][h * 4 + e];
+        float *cp = pr.C + (int64_t)row * pr.ldc + col;
+        const float *cin = pr.C_in ? pr.C_in + (int64_t)row * pr.ldc + col : nullptr;
+        if (pr.c_vec && col + 4 <= pr.N) {
+          if (pr.beta != 0.f) {
+            float4 c = *reinterpret_cast<const float4 *>(cin);
+            o[0] += pr.beta * c.x; o[1] += pr.beta * c.y; o[2] += pr.beta * c.z; o[3] += pr.beta * c.w;
+          }
+          *reinterpret_cast<float4 *>(cp) = make_float4(o[0], o[1], o[2], o[3]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (col + e < pr.N) {
+              float r = o[e];
+              if (pr.beta != 0.f) r += pr.beta * cin[e];
+              cp[e] = r;
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+template <int MAXP>
+cudaError_t launch_simt_f32(const SimtParams<MAXP> &p, int grid, cudaStream_t st) {
+  sk_simt_f32_kernel<MAXP><<<grid, F32_THREADS, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_simt_f32<1>(const SimtParams<1> &, int, cudaStream_t);
+template cudaError_t launch_simt_f32<MAXP_GROUPED>(const SimtParams<MAXP_GROUPED> &, int, cudaStream_t);
+
+}  // namespace sk

@@ -1,0 +1,425 @@
+// Stream-K GEMM on the 5th-generation tensor cores (tcgen05), sm_103a.
+//
+// One persistent CTA per unit (192 threads, 1 CTA per SM):
+//   warp 0 (lane 0) : TMA producer.  For every k-block of every item it waits
+//                     for a free ring slot, then loads the 128 x BK slice of A
+//                     and the BN x BK slice of B (128-byte swizzled rows) into
+//                     shared memory, completing on the slot's `full` mbarrier.
+//   warp 1          : allocates TMEM (2 accumulators of BN fp32 columns);
+//                     lane 0 issues tcgen05.mma (M=128, N=BN) per k-block into
+//                     the current accumulator, frees ring slots with
+//                     tcgen05.commit, and signals `tmem_full` per item.
+//   warps 2-5       : epilogue.  Each thread owns one accumulator row (TMEM
+//                     lane).  By role: peer -> FP32 partial to the workspace
+//                     + release flag; owner -> bounded acquire-wait on the
+//                     peers' flags, add their partials in ascending CTA order;
+//                     then C = alpha*acc + beta*C_in, rounded to the output
+//                     type and stored with bounds masks (no padding).
+// Two accumulators let the epilogue of item i overlap the MMAs of item i+1.
+// All three roles walk the same item sequence from the shared scheduler.
+//
+// Every wait is bounded (timeout_ns of %globaltimer).  On expiry the kernel
+// records STATUS_TIMEOUT in the workspace status word, raises a CTA-wide
+// abort flag so the other roles stop issuing work, drains what it issued,
+// frees TMEM and returns.
+#pragma once
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "ptx.cuh"
+
+namespace sk {
+
+template <int IN>
+struct InTraits;
+template <>
+struct InTraits<IN_BF16> {
+  static constexpr int BK = 64;       // elements per k-block (128 bytes)
+  static constexpr int UMMA_K = 16;   // K of one tcgen05.mma kind::f16
+  // D f32 (bit 4), A bf16 (bits 7-9 = 1), B bf16 (bits 10-12 = 1)
+  static constexpr uint32_t IDESC_TYPES = (1u << 4) | (1u << 7) | (1u << 10);
+};
+template <>
+struct InTraits<IN_E4M3> {
+  static constexpr int BK = 128;
+  static constexpr int UMMA_K = 32;   // K of one tcgen05.mma kind::f8f6f4
+  // D f32, A e4m3 (0), B e4m3 (0)
+  static constexpr uint32_t IDESC_TYPES = (1u << 4);
+};
+
+template <typename OutT>
+struct OutStore;
+
+template <>
+struct OutStore<float> {
+  // 32 consecutive outputs of one row.
+  __device__ static __forceinline__ void run(const TcProblem &pr, int row, int col, const float (&v)[32],
+                                             float alpha) {
+    float *cp = static_cast<float *>(pr.C) + (int64_t)row * pr.ldc + col;
+    const float *ci = pr.beta != 0.f ? static_cast<const float *>(pr.C_in) + (int64_t)row * pr.ldc + col : nullptr;
+    if (pr.c_vec && col + 32 <= pr.N) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        float4 o = make_float4(alpha * v[4 * j], alpha * v[4 * j + 1], alpha * v[4 * j + 2], alpha * v[4 * j + 3]);
+        if (ci) {
+          float4 c = *reinterpret_cast<const float4 *>(ci + 4 * j);
+          o.x += pr.beta * c.x; o.y += pr.beta * c.y; o.z += pr.beta * c.z; o.w += pr.beta * c.w;
+        }
+        *reinterpret_cast<float4 *>(cp + 4 * j) = o;
+      }
+    } else {
+      for (int j = 0; j < 32 && col + j < pr.N; ++j) {
+        float o = alpha * v[j];
+        if (ci) o += pr.beta * ci[j];
+        cp[j] = o;
+      }
+    }
+  }
+};
+
+template <>
+struct OutStore<__nv_bfloat16> {
+  __device__ static __forceinline__ void run(const TcProblem &pr, int row, int col, const float (&v)[32],
+                                             float alpha) {
+    __nv_bfloat16 *cp = static_cast<__nv_bfloat16 *>(pr.C) + (int64_t)row * pr.ldc + col;
+    const __nv_bfloat16 *ci =
+        pr.beta != 0.f ? static_cast<const __nv_bfloat16 *>(pr.C_in) + (int64_t)row * pr.ldc + col : nullptr;
+    if (pr.c_vec && col + 32 <= pr.N) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float o[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = alpha * v[8 * j + e];
+        if (ci) {
+          uint4 raw = *reinterpret_cast<const uint4 *>(ci + 8 * j);
+          const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&raw);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float2 f = __bfloat1622float2(h[e]);
+            o[2 * e] += pr.beta * f.x;
+            o[2 * e + 1] += pr.beta * f.y;
+          }
+        }
+        uint4 packed;
+        __nv_bfloat162 *ph = reinterpret_cast<__nv_bfloat162 *>(&packed);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ph[e] = __floats2bfloat162_rn(o[2 * e], o[2 * e + 1]);
+        *reinterpret_cast<uint4 *>(cp + 8 * j) = packed;
+      }
+    } else {
+      for (int j = 0; j < 32 && col + j < pr.N; ++j) {
+        float o = alpha * v[j];
+        if (ci) o += pr.beta * __bfloat162float(ci[j]);
+        cp[j] = __float2bfloat16_rn(o);
+      }
+    }
+  }
+};
+
+template <int IN, typename OutT, int BN, int MAXP>
+__global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ TcParams<MAXP> P) {
+  using Tr = InTraits<IN>;
+  constexpr int BM = 128;
+  constexpr int BK = Tr::BK;
+  constexpr int UMMA_K = Tr::UMMA_K;
+  constexpr int A_BYTES = BM * 128;
+  constexpr int B_BYTES = BN * 128;
+  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr int MN_CHUNK_BYTES = BK * 128;   // one 64-wide MN chunk of an MN-major slice
+  constexpr uint32_t IDESC = Tr::IDESC_TYPES | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "tile N");
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw_addr = smem_u32(smem_raw);
+  uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
+  const int stages = P.stages;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + stages * STAGE_BYTES);
+  uint64_t *full_bar = bars;
+  uint64_t *empty_bar = bars + stages;
+  uint64_t *tfull_bar = bars + 2 * stages;
+  uint64_t *tempty_bar = tfull_bar + 2;
+  uint64_t *done_bar = tempty_bar + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
+  volatile uint32_t *abort_flag = tmem_slot + 1;
+  const uint32_t tiles_addr = smem_u32(smem);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int u = blockIdx.x;
+  const Sched &S = P.sched;
+  const uint64_t tmo = P.timeout_ns;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) {
+      mbar_init(smem_u32(full_bar + s), 1);
+      mbar_init(smem_u32(empty_bar + s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(tfull_bar + a), 1);
+      mbar_init(smem_u32(tempty_bar + a), 4);
+    }
+    mbar_init(smem_u32(done_bar), 1);
+    *abort_flag = 0;
+    fence_barrier_init();
+    fence_proxy_async_smem();
+  }
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicExch(P.ws.status, STATUS_TIMEOUT);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      const int np = S.num_problems < MAXP ? S.num_problems : MAXP;
+      for (int p = 0; p < np && p < 4; ++p) {
+        tma_prefetch_desc(&P.prob[p].tmap_a);
+        tma_prefetch_desc(&P.prob[p].tmap_b);
+      }
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t loads = 0;
+      Cursor c;
+      cursor_init(S, u, c);
+      Item w;
+      bool ok = true;
+      while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
+        const TcProblem &pr = P.prob[w.problem];
+        const int m0 = w.tm * BM, n0 = w.tn * BN;
+        for (int kb = w.k0; kb < w.k1; ++kb) {
+          if (!mbar_wait(smem_u32(empty_bar + stage), phase ^ 1u, tmo) || *abort_flag) {
+            ok = false;
+            break;
+          }
+          const uint32_t fb = smem_u32(full_bar + stage);
+          mbar_arrive_expect_tx(fb, STAGE_BYTES);
+          const uint32_t sa = tiles_addr + stage * STAGE_BYTES;
+          const uint32_t sb = sa + A_BYTES;
+          const int kx = kb * BK;
+          if (!pr.a_mn) {
+            tma_load_2d(sa, &pr.tmap_a, fb, kx, m0);
+          } else {
+#pragma unroll
+            for (int ch = 0; ch < BM / 64; ++ch) tma_load_2d(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fb, m0 + 64 * ch, kx);
+          }
+          if (!pr.b_mn) {
+            tma_load_2d(sb, &pr.tmap_b, fb, kx, n0);
+          } else {
+#pragma unroll
+            for (int ch = 0; ch < BN / 64; ++ch) tma_load_2d(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fb, n0 + 64 * ch, kx);
+          }
+          ++loads;
+          if (++stage == stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) fail();
+      // Drain (bounded): every issued TMA load must land before the CTA may
+      // exit -- slot s last completed phase `phase` if s < stage, else the
+      // phase before -- and, on the normal path, every slot must have been
+      // released by the MMA warp's commits.
+      for (int s = 0; s < stages && s < loads; ++s) {
+        const uint32_t par = s < stage ? phase : (phase ^ 1u);
+        if (!mbar_wait(smem_u32(full_bar + s), par, tmo)) {
+          fail();
+          break;
+        }
+      }
+      for (int i = 0; i < stages && !*abort_flag; ++i) {
+        if (!mbar_wait(smem_u32(empty_bar + stage), phase ^ 1u, tmo)) {
+          fail();
+          break;
+        }
+        if (++stage == stages) {
+          stage = 0;
+          phase ^= 1u;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int acc = 0;
+      uint32_t acc_phase = 0;
+      Cursor c;
+      cursor_init(S, u, c);
+      Item w;
+      bool ok = true;
+      while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
+        const TcProblem &pr = P.prob[w.problem];
+        const uint32_t idesc = IDESC | ((uint32_t)pr.a_mn << 15) | ((uint32_t)pr.b_mn << 16);
+        if (!mbar_wait(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+        for (int kb = w.k0; kb < w.k1; ++kb) {
+          if (!mbar_wait(smem_u32(full_bar + stage), phase, tmo)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = tiles_addr + stage * STAGE_BYTES;
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+            // K-major: advance 32 bytes along the swizzled row per UMMA_K;
+            // MN-major: advance UMMA_K rows of 128 bytes.
+            const uint64_t ad = pr.a_mn ? smem_desc_sw128(sa + kk * UMMA_K * 128, MN_CHUNK_BYTES, 1024)
+                                        : smem_desc_sw128(sa + kk * 32, 16, 1024);
+            const uint64_t bd = pr.b_mn ? smem_desc_sw128(sb + kk * UMMA_K * 128, MN_CHUNK_BYTES, 1024)
+                                        : smem_desc_sw128(sb + kk * 32, 16, 1024);
+            const uint32_t accum = (kb > w.k0 || kk > 0) ? 1u : 0u;
+            if constexpr (IN == IN_BF16)
+              mma_f16(d_tmem, ad, bd, idesc, accum);
+            else
+              mma_f8(d_tmem, ad, bd, idesc, accum);
+          }
+          mma_commit(smem_u32(empty_bar + stage));
+          if (++stage == stages) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(tfull_bar + acc));
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1u;
+        }
+      }
+      if (!ok) fail();
+      // All MMAs issued by this thread are complete once done_bar flips.
+      mma_commit(smem_u32(done_bar));
+      if (!mbar_wait(smem_u32(done_bar), 0u, tmo)) fail();
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = warp & 3;                 // TMEM lane quarter this warp may access
+    const int row = q4 * 32 + lane;          // accumulator row of this thread
+    const int et = threadIdx.x - 64;         // 0..127
+    float4 *slots = reinterpret_cast<float4 *>(P.ws.partials);
+    constexpr int64_t SLOT_F4 = (int64_t)BM * BN / 4;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    Cursor c;
+    cursor_init(S, u, c);
+    Item w;
+    while (!*abort_flag && cursor_next(S, P.ps, u, c, w)) {
+      const TcProblem &pr = P.prob[w.problem];
+      if (!mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo)) {
+        fail();
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tbase = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN);
+
+      if (w.role == ROLE_PEER) {
+        float4 *slot = slots + (int64_t)u * SLOT_F4;
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 32; ++ch) {
+          float v[32];
+          tmem_ld32(tbase + ch * 32, v);
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            __stcg(slot + (ch * 8 + j) * 128 + row, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(tempty_bar + acc));
+        __threadfence();
+        named_bar_sync(1, 128);
+        if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + u, 1u);
+      } else {
+        if (w.role == ROLE_OWNER) {
+          if (et == 0) {
+            const uint64_t t0 = globaltimer();
+            bool to = false;
+            for (int p = w.peer_first; p <= w.peer_last && !to; ++p) {
+              while (ld_acquire_gpu(P.ws.flags + p) == 0u) {
+                if (globaltimer() - t0 > tmo) {
+                  atomicExch(P.ws.status, STATUS_TIMEOUT);
+                  to = true;
+                  break;
+                }
+              }
+            }
+          }
+          named_bar_sync(1, 128);
+        }
+        float alpha = pr.alpha;
+        if (IN == IN_E4M3) {
+          if (pr.scale_a) alpha *= *pr.scale_a;
+          if (pr.scale_b) alpha *= *pr.scale_b;
+        }
+        const int grow = w.tm * BM + row;
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 32; ++ch) {
+          float v[32];
+          tmem_ld32(tbase + ch * 32, v);
+          if (w.role == ROLE_OWNER) {
+            // Fixed order: own accumulator, then peers in ascending CTA index.
+            for (int p = w.peer_first; p <= w.peer_last; ++p) {
+              const float4 *slot = slots + (int64_t)p * SLOT_F4;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                float4 q = __ldcg(slot + (ch * 8 + j) * 128 + row);
+                v[4 * j] += q.x;
+                v[4 * j + 1] += q.y;
+                v[4 * j + 2] += q.z;
+                v[4 * j + 3] += q.w;
+              }
+            }
+          }
+          if (grow < pr.M) {
+            const int gcol = w.tn * BN + ch * 32;
+            if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(tempty_bar + acc));
+        if (w.role == ROLE_OWNER && et == 0)
+          for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[p] = 0u;
+      }
+      if (++acc == 2) {
+        acc = 0;
+        acc_phase ^= 1u;
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+template <int IN, typename OutT, int BN, int MAXP>
+cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP>;
+  const int smem = tc_smem_bytes(BN, p.stages);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 192, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace sk

@@ -1,0 +1,712 @@
+// C-ABI layer of the Stream-K GEMM: argument checks, layout normalisation,
+// the Stream-K / hybrid plan, workspace carving, TMA descriptor encoding and
+// kernel launch.  See include/skgemm.h for the contract of every entry point.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/skgemm.h"
+#include "common.cuh"
+
+using namespace sk;
+
+namespace {
+
+// ------------------------------------------------------------------ device
+struct DevInfo {
+  bool ready = false;
+  int sms = 0;
+  int major = 0, minor = 0;
+};
+std::mutex g_mu;
+DevInfo g_dev[64];
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn g_encode = nullptr;
+
+sk_status current_device(int *dev, DevInfo *out) {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess) return SK_ERR_NO_DEVICE;
+  if (d < 0 || d >= 64) return SK_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> lk(g_mu);
+  DevInfo &di = g_dev[d];
+  if (!di.ready) {
+    if (cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, d) != cudaSuccess) return SK_ERR_NO_DEVICE;
+    cudaDeviceGetAttribute(&di.major, cudaDevAttrComputeCapabilityMajor, d);
+    cudaDeviceGetAttribute(&di.minor, cudaDevAttrComputeCapabilityMinor, d);
+    di.ready = true;
+  }
+  *dev = d;
+  *out = di;
+  return SK_OK;
+}
+
+sk_status encoder(EncodeTiledFn *fn) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_encode) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+      return SK_ERR_CUDA;
+    g_encode = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *fn = g_encode;
+  return SK_OK;
+}
+
+// --------------------------------------------------------- problem checks
+int dtype_bytes(sk_dtype t) {
+  switch (t) {
+    case SK_F32: return 4;
+    case SK_BF16: return 2;
+    case SK_E4M3: return 1;
+  }
+  return 0;
+}
+
+bool valid_layout(sk_layout l) { return l == SK_ROW_MAJOR || l == SK_COL_MAJOR; }
+bool valid_dtype(sk_dtype t) { return t == SK_F32 || t == SK_BF16 || t == SK_E4M3; }
+sk_layout flip(sk_layout l) { return l == SK_ROW_MAJOR ? SK_COL_MAJOR : SK_ROW_MAJOR; }
+
+// Minimum leading dimension of an r x c matrix stored with layout l.
+int64_t min_ld(sk_layout l, int64_t r, int64_t c) {
+  int64_t e = l == SK_ROW_MAJOR ? c : r;
+  return e < 1 ? 1 : e;
+}
+
+// Kernel family of a type combination.
+enum Family { FAM_F32 = 0, FAM_BF16 = 1, FAM_E4M3 = 2, FAM_NONE = -1 };
+
+Family family_of(const sk_problem &p) {
+  if (p.a_type != p.b_type) return FAM_NONE;
+  if (p.a_type == SK_F32) return p.c_type == SK_F32 ? FAM_F32 : FAM_NONE;
+  if (p.a_type == SK_BF16) return (p.c_type == SK_BF16 || p.c_type == SK_F32) ? FAM_BF16 : FAM_NONE;
+  if (p.a_type == SK_E4M3) return (p.c_type == SK_BF16 || p.c_type == SK_F32) ? FAM_E4M3 : FAM_NONE;
+  return FAM_NONE;
+}
+
+sk_status check_problem(const sk_problem *p) {
+  if (!p) return SK_ERR_INVALID_ARG;
+  if (p->m < 0 || p->n < 0 || p->k < 0) return SK_ERR_INVALID_ARG;
+  if (p->m > INT32_MAX / 2 || p->n > INT32_MAX / 2 || p->k > INT32_MAX / 2) return SK_ERR_UNSUPPORTED;
+  if (!valid_dtype(p->a_type) || !valid_dtype(p->b_type) || !valid_dtype(p->c_type)) return SK_ERR_INVALID_ARG;
+  if (!valid_layout(p->a_layout) || !valid_layout(p->b_layout) || !valid_layout(p->c_layout))
+    return SK_ERR_INVALID_ARG;
+  if (family_of(*p) == FAM_NONE) return SK_ERR_UNSUPPORTED;
+  if (p->m == 0 || p->n == 0) return SK_OK;
+  if (!p->C) return SK_ERR_INVALID_ARG;
+  if (p->ldc < min_ld(p->c_layout, p->m, p->n)) return SK_ERR_INVALID_ARG;
+  if (p->beta != 0.f && !p->C_in) return SK_ERR_INVALID_ARG;
+  if (p->k == 0) return SK_OK;
+  if (!p->A || !p->B) return SK_ERR_INVALID_ARG;
+  if (p->lda < min_ld(p->a_layout, p->m, p->k)) return SK_ERR_INVALID_ARG;
+  if (p->ldb < min_ld(p->b_layout, p->k, p->n)) return SK_ERR_INVALID_ARG;
+  return SK_OK;
+}
+
+// A problem rewritten so that C is row-major: C col-major (m x n) is the
+// row-major C^T (n x m) = B^T A^T, with each transpose a layout flip.
+struct Norm {
+  int64_t M, N, K;
+  const void *A, *B;
+  const void *C_in;
+  void *C;
+  sk_layout a_layout, b_layout;   // of the (possibly swapped) operands
+  int64_t lda, ldb, ldc;
+  float alpha, beta;
+  const float *sa, *sb;
+  sk_dtype in_type, c_type;
+};
+
+Norm normalise(const sk_problem &p) {
+  Norm n;
+  n.alpha = p.alpha;
+  n.beta = p.beta;
+  n.sa = p.scale_a;
+  n.sb = p.scale_b;
+  n.in_type = p.a_type;
+  n.c_type = p.c_type;
+  n.C = p.C;
+  n.C_in = p.C_in;
+  n.ldc = p.ldc;
+  n.K = p.k;
+  if (p.c_layout == SK_ROW_MAJOR) {
+    n.M = p.m;
+    n.N = p.n;
+    n.A = p.A;
+    n.a_layout = p.a_layout;
+    n.lda = p.lda;
+    n.B = p.B;
+    n.b_layout = p.b_layout;
+    n.ldb = p.ldb;
+  } else {
+    n.M = p.n;
+    n.N = p.m;
+    n.A = p.B;
+    n.a_layout = flip(p.b_layout);
+    n.lda = p.ldb;
+    n.B = p.A;
+    n.b_layout = flip(p.a_layout);
+    n.ldb = p.lda;
+    std::swap(n.sa, n.sb);
+  }
+  return n;
+}
+
+// ------------------------------------------------------------------ config
+struct Cfg {
+  Family fam;
+  int BM, BN, BK, stages;
+  sk_mode mode;
+  int g;
+  int min_ipu;
+  uint64_t timeout_ns;
+  int debug_flags;
+};
+
+sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
+  sk_config d;
+  std::memset(&d, 0, sizeof(d));
+  if (c) d = *c;
+  Cfg r;
+  r.fam = fam;
+  if (d.tile_m != 0 && d.tile_m != 128) return SK_ERR_UNSUPPORTED;
+  r.BM = 128;
+  if (fam == FAM_F32) {
+    if (d.tile_n != 0 && d.tile_n != 128) return SK_ERR_UNSUPPORTED;
+    r.BN = 128;
+    r.BK = F32_BK;
+    if (d.stages != 0 && d.stages != 2) return SK_ERR_UNSUPPORTED;
+    r.stages = 2;
+  } else {
+    r.BN = d.tile_n ? d.tile_n : 256;
+    if (r.BN != 128 && r.BN != 256) return SK_ERR_UNSUPPORTED;
+    r.BK = fam == FAM_BF16 ? 64 : 128;
+    const int stage_bytes = 128 * 128 + r.BN * 128;
+    const int max_stages = std::min(6, (227 * 1024 - 1024 - 256) / stage_bytes);
+    r.stages = d.stages ? d.stages : max_stages;
+    if (r.stages < 2 || r.stages > max_stages) return SK_ERR_UNSUPPORTED;
+  }
+  if (d.mode < SK_MODE_AUTO || d.mode > SK_MODE_HYBRID2) return SK_ERR_INVALID_ARG;
+  r.mode = d.mode == SK_MODE_AUTO ? SK_MODE_HYBRID2 : d.mode;
+  if (sms <= 0) return SK_ERR_INVALID_ARG;
+  if (d.num_ctas < 0 || d.num_ctas > sms) return SK_ERR_INVALID_ARG;
+  r.g = d.num_ctas ? d.num_ctas : sms;
+  if (d.min_iters_per_unit < 0) return SK_ERR_INVALID_ARG;
+  r.min_ipu = d.min_iters_per_unit ? d.min_iters_per_unit : 4;
+  r.timeout_ns = d.timeout_ns ? d.timeout_ns : 2000000000ull;
+  r.debug_flags = d.debug_flags;
+  *out = r;
+  return SK_OK;
+}
+
+size_t ws_bytes_for(const Cfg &c) {
+  const size_t flags = ((size_t)c.g * 4 + 255) / 256 * 256;
+  return 256 + flags + (size_t)c.g * c.BM * c.BN * 4;
+}
+
+Workspace carve(void *ws, const Cfg &c) {
+  uint8_t *b = static_cast<uint8_t *>(ws);
+  Workspace w;
+  w.status = reinterpret_cast<uint32_t *>(b);
+  w.flags = reinterpret_cast<uint32_t *>(b + 256);
+  const size_t flags = ((size_t)c.g * 4 + 255) / 256 * 256;
+  w.partials = reinterpret_cast<float *>(b + 256 + flags);
+  return w;
+}
+
+// -------------------------------------------------------------------- plan
+struct PlanOut {
+  Sched s;
+  std::vector<ProbSched> ps;
+  std::vector<int> orig_index;   // problem index in the caller's array
+  int grid;
+};
+
+int64_t count_sk_tiles(int64_t T, int64_t g, sk_mode mode) {
+  switch (mode) {
+    case SK_MODE_DP: return 0;
+    case SK_MODE_SK: return T;
+    case SK_MODE_HYBRID1: return T % g;
+    case SK_MODE_HYBRID2:
+      if (T <= g) return T;
+      if (T % g == 0) return 0;
+      return g + T % g;
+    default: return T;
+  }
+}
+
+// Builds the plan over the problems with m, n, k >= 1 (in their order).
+void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, const Cfg &c, PlanOut *out) {
+  out->ps.clear();
+  out->orig_index.clear();
+  int64_t tiles = 0, iters = 0;
+  for (size_t i = 0; i < probs.size(); ++i) {
+    const Norm &n = probs[i];
+    ProbSched p;
+    p.tiles_m = (int32_t)((n.M + c.BM - 1) / c.BM);
+    p.tiles_n = (int32_t)((n.N + c.BN - 1) / c.BN);
+    p.iters = (int32_t)((n.K + c.BK - 1) / c.BK);
+    p.pad_ = 0;
+    p.tile_base = tiles;
+    p.iter_base = iters;
+    const int64_t t = (int64_t)p.tiles_m * p.tiles_n;
+    tiles += t;
+    iters += t * p.iters;
+    out->ps.push_back(p);
+    out->orig_index.push_back(idx[i]);
+  }
+  Sched &s = out->s;
+  s.num_problems = (int32_t)out->ps.size();
+  s.g = c.g;
+  s.total_tiles = tiles;
+  s.sk_tiles = count_sk_tiles(tiles, c.g, c.mode);
+  // iterations of the leading sk_tiles tiles
+  int64_t ski = 0;
+  for (const ProbSched &p : out->ps) {
+    const int64_t t = (int64_t)p.tiles_m * p.tiles_n;
+    const int64_t lo = p.tile_base, hi = p.tile_base + t;
+    const int64_t take = std::max<int64_t>(0, std::min(hi, s.sk_tiles) - lo);
+    ski += take * p.iters;
+  }
+  s.sk_iters = ski;
+  if (ski > 0) {
+    int64_t units = ski / std::max(1, c.min_ipu);
+    units = std::max<int64_t>(1, std::min<int64_t>(c.g, units));
+    s.sk_units = (int32_t)units;
+    s.q = ski / units;
+    s.r = (int32_t)(ski % units);
+  } else {
+    s.sk_units = 0;
+    s.q = 0;
+    s.r = 0;
+  }
+  const int64_t dp = tiles - s.sk_tiles;
+  out->grid = (int)std::max<int64_t>(s.sk_units, std::min<int64_t>(c.g, dp));
+}
+
+// --------------------------------------------------------------- launches
+sk_status cuda_err(cudaError_t e) { return e == cudaSuccess ? SK_OK : SK_ERR_CUDA; }
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+sk_status check_tc_alignment(const Norm &n) {
+  const int es = dtype_bytes(n.in_type);
+  if (!aligned16(n.A) || !aligned16(n.B)) return SK_ERR_UNSUPPORTED;
+  if ((n.lda * es) % 16 != 0 || (n.ldb * es) % 16 != 0) return SK_ERR_UNSUPPORTED;
+  if (n.in_type == SK_E4M3 && (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR)) return SK_ERR_UNSUPPORTED;
+  return SK_OK;
+}
+
+sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk_dtype t, bool kmajor, int64_t rows,
+                         int64_t K, int64_t ld, int box_rows, int BK) {
+  const int es = dtype_bytes(t);
+  const CUtensorMapDataType dt = t == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  cuuint64_t dims[2], strides[1];
+  cuuint32_t box[2], estr[2] = {1, 1};
+  if (kmajor) {   // element (r, k) at base[r*ld + k]
+    dims[0] = (cuuint64_t)K;
+    dims[1] = (cuuint64_t)rows;
+    box[0] = (cuuint32_t)BK;
+    box[1] = (cuuint32_t)box_rows;
+  } else {        // element (r, k) at base[r + k*ld]
+    dims[0] = (cuuint64_t)rows;
+    dims[1] = (cuuint64_t)K;
+    box[0] = 64;
+    box[1] = (cuuint32_t)BK;
+  }
+  strides[0] = (cuuint64_t)ld * es;
+  CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_CUDA;
+}
+
+template <int MAXP>
+sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, const Cfg &c, Workspace ws,
+                           cudaStream_t st) {
+  EncodeTiledFn enc;
+  sk_status rc = encoder(&enc);
+  if (rc != SK_OK) return rc;
+  // Heap-allocated: the grouped parameter block is ~22 KB.
+  TcParams<MAXP> *P = new TcParams<MAXP>();
+  std::memset(P, 0, sizeof(*P));
+  const size_t np = probs.size();
+  for (size_t i = 0; i < np; ++i) {
+    const Norm &n = probs[i];
+    TcProblem &tp = P->prob[i];
+    const bool a_k = n.a_layout == SK_ROW_MAJOR;   // A(i,k) at A[i*lda + k]
+    const bool b_k = n.b_layout == SK_COL_MAJOR;   // B(k,j) at B[k + j*ldb]
+    rc = encode_operand(enc, &tp.tmap_a, n.A, n.in_type, a_k, n.M, n.K, n.lda, 128, c.BK);
+    if (rc == SK_OK) rc = encode_operand(enc, &tp.tmap_b, n.B, n.in_type, b_k, n.N, n.K, n.ldb, c.BN, c.BK);
+    if (rc != SK_OK) {
+      delete P;
+      return rc;
+    }
+    tp.C = n.C;
+    tp.C_in = n.C_in;
+    tp.ldc = n.ldc;
+    tp.M = (int32_t)n.M;
+    tp.N = (int32_t)n.N;
+    tp.K = (int32_t)n.K;
+    tp.alpha = n.alpha;
+    tp.beta = n.beta;
+    tp.a_mn = a_k ? 0 : 1;
+    tp.b_mn = b_k ? 0 : 1;
+    const int ces = n.c_type == SK_F32 ? 4 : 2;
+    tp.c_vec = aligned16(n.C) && (n.beta == 0.f || aligned16(n.C_in)) && ((n.ldc * ces) % 16 == 0);
+    tp.scale_a = n.sa;
+    tp.scale_b = n.sb;
+    P->ps[i] = pl.ps[i];
+  }
+  P->sched = pl.s;
+  P->ws = ws;
+  P->timeout_ns = c.timeout_ns;
+  P->stages = c.stages;
+  P->debug_flags = c.debug_flags;
+  const bool f32out = probs[0].c_type == SK_F32;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (c.fam == FAM_BF16) {
+    if (c.BN == 256)
+      e = f32out ? launch_tc<IN_BF16, float, 256, MAXP>(*P, pl.grid, st)
+                 : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP>(*P, pl.grid, st);
+    else
+      e = f32out ? launch_tc<IN_BF16, float, 128, MAXP>(*P, pl.grid, st)
+                 : launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP>(*P, pl.grid, st);
+  } else if (c.fam == FAM_E4M3) {
+    if constexpr (MAXP == 1) {
+      if (c.BN == 256)
+        e = f32out ? launch_tc<IN_E4M3, float, 256, 1>(*P, pl.grid, st)
+                   : launch_tc<IN_E4M3, __nv_bfloat16, 256, 1>(*P, pl.grid, st);
+      else
+        e = f32out ? launch_tc<IN_E4M3, float, 128, 1>(*P, pl.grid, st)
+                   : launch_tc<IN_E4M3, __nv_bfloat16, 128, 1>(*P, pl.grid, st);
+    } else {
+      delete P;
+      return SK_ERR_UNSUPPORTED;
+    }
+  }
+  delete P;
+  return cuda_err(e);
+}
+
+template <int MAXP>
+sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, const Cfg &c, Workspace ws,
+                            cudaStream_t st) {
+  SimtParams<MAXP> *P = new SimtParams<MAXP>();
+  std::memset(P, 0, sizeof(*P));
+  for (size_t i = 0; i < probs.size(); ++i) {
+    const Norm &n = probs[i];
+    SimtProblem &sp = P->prob[i];
+    sp.A = static_cast<const float *>(n.A);
+    sp.B = static_cast<const float *>(n.B);
+    sp.C_in = static_cast<const float *>(n.C_in);
+    sp.C = static_cast<float *>(n.C);
+    if (n.a_layout == SK_ROW_MAJOR) {
+      sp.a_rs = n.lda;
+      sp.a_cs = 1;
+    } else {
+      sp.a_rs = 1;
+      sp.a_cs = n.lda;
+    }
+    if (n.b_layout == SK_ROW_MAJOR) {
+      sp.b_rs = n.ldb;
+      sp.b_cs = 1;
+    } else {
+      sp.b_rs = 1;
+      sp.b_cs = n.ldb;
+    }
+    sp.ldc = n.ldc;
+    sp.M = (int32_t)n.M;
+    sp.N = (int32_t)n.N;
+    sp.K = (int32_t)n.K;
+    sp.alpha = n.alpha;
+    sp.beta = n.beta;
+    sp.a_kmajor = n.a_layout == SK_ROW_MAJOR;
+    sp.b_kmajor = n.b_layout == SK_COL_MAJOR;
+    sp.a_vec = aligned16(n.A) && (n.lda % 4 == 0);
+    sp.b_vec = aligned16(n.B) && (n.ldb % 4 == 0);
+    sp.c_vec = aligned16(n.C) && (n.beta == 0.f || aligned16(n.C_in)) && (n.ldc % 4 == 0);
+    P->ps[i] = pl.ps[i];
+  }
+  P->sched = pl.s;
+  P->ws = ws;
+  P->timeout_ns = c.timeout_ns;
+  P->debug_flags = c.debug_flags;
+  cudaError_t e = launch_simt_f32<MAXP>(*P, pl.grid, st);
+  delete P;
+  return cuda_err(e);
+}
+
+// Shared driver of sk_gemm / sk_gemm_grouped / sk_gemm_backward.
+sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void *ws, size_t ws_bytes,
+              cudaStream_t st, int maxp) {
+  if (!problems || count < 1 || count > maxp) return SK_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    sk_status rc = check_problem(&problems[i]);
+    if (rc != SK_OK) return rc;
+  }
+  const Family fam = family_of(problems[0]);
+  for (int i = 1; i < count; ++i)
+    if (problems[i].a_type != problems[0].a_type || problems[i].c_type != problems[0].c_type)
+      return SK_ERR_UNSUPPORTED;
+  int dev;
+  DevInfo di;
+  sk_status rc = current_device(&dev, &di);
+  if (rc != SK_OK) return rc;
+  if (!(di.major == 10 && di.minor == 3)) return SK_ERR_NO_DEVICE;   // built for sm_103a only
+  Cfg c;
+  rc = resolve_cfg(fam, cfg, di.sms, &c);
+  if (rc != SK_OK) return rc;
+
+  // Validate everything before launching anything.
+  std::vector<Norm> work, scale_only;
+  std::vector<int> idx;
+  for (int i = 0; i < count; ++i) {
+    const sk_problem &p = problems[i];
+    if (p.m == 0 || p.n == 0) continue;
+    Norm n = normalise(p);
+    if (p.k == 0) {
+      scale_only.push_back(n);   // C = beta * C_in: nothing to accumulate
+      continue;
+    }
+    if (fam != FAM_F32) {
+      rc = check_tc_alignment(n);
+      if (rc != SK_OK) return rc;
+    }
+    work.push_back(n);
+    idx.push_back(i);
+  }
+  if (!work.empty()) {
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return SK_ERR_INVALID_ARG;
+    if (ws_bytes < ws_bytes_for(c)) return SK_ERR_WORKSPACE_TOO_SMALL;
+  }
+  for (const Norm &n : scale_only) {
+    rc = cuda_err(launch_scale(n.C, n.C_in, n.ldc, n.M, n.N, n.beta, n.c_type == SK_F32, st));
+    if (rc != SK_OK) return rc;
+  }
+  if (work.empty()) return SK_OK;
+  PlanOut pl;
+  build_plan(work, idx, c, &pl);
+  Workspace w = carve(ws, c);
+  if (fam == FAM_F32) {
+    return work.size() == 1 && maxp == 1 ? launch_f32_family<1>(work, pl, c, w, st)
+                                         : launch_f32_family<MAXP_GROUPED>(work, pl, c, w, st);
+  }
+  return work.size() == 1 && maxp == 1 ? launch_tc_family<1>(work, pl, c, w, st)
+                                       : launch_tc_family<MAXP_GROUPED>(work, pl, c, w, st);
+}
+
+// Plan for queries: honours num_sms > 0 without touching a device.
+sk_status plan_for_query(const sk_problem *problems, int count, const sk_config *cfg, int num_sms, Cfg *c,
+                         PlanOut *pl) {
+  if (!problems || count < 1 || count > MAXP_GROUPED) return SK_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i) {
+    sk_status rc = check_problem(&problems[i]);
+    if (rc != SK_OK) return rc;
+  }
+  const Family fam = family_of(problems[0]);
+  int sms = num_sms;
+  if (sms <= 0) {
+    int dev;
+    DevInfo di;
+    sk_status rc = current_device(&dev, &di);
+    if (rc != SK_OK) return rc;
+    sms = di.sms;
+  }
+  sk_status rc = resolve_cfg(fam, cfg, sms, c);
+  if (rc != SK_OK) return rc;
+  std::vector<Norm> work;
+  std::vector<int> idx;
+  for (int i = 0; i < count; ++i) {
+    const sk_problem &p = problems[i];
+    if (p.m == 0 || p.n == 0 || p.k == 0) continue;
+    work.push_back(normalise(p));
+    idx.push_back(i);
+  }
+  build_plan(work, idx, *c, pl);
+  return SK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sk_version(void) { return "skgemm 0.1 (sm_103a)"; }
+
+const char *sk_status_string(sk_status s) {
+  switch (s) {
+    case SK_OK: return "SK_OK";
+    case SK_ERR_INVALID_ARG: return "SK_ERR_INVALID_ARG";
+    case SK_ERR_UNSUPPORTED: return "SK_ERR_UNSUPPORTED";
+    case SK_ERR_WORKSPACE_TOO_SMALL: return "SK_ERR_WORKSPACE_TOO_SMALL";
+    case SK_ERR_TIMEOUT: return "SK_ERR_TIMEOUT";
+    case SK_ERR_CUDA: return "SK_ERR_CUDA";
+    case SK_ERR_NO_DEVICE: return "SK_ERR_NO_DEVICE";
+  }
+  return "SK_ERR_UNKNOWN";
+}
+
+sk_status sk_workspace_size(const sk_problem *problems, int count, const sk_config *cfg, size_t *bytes) {
+  if (!bytes) return SK_ERR_INVALID_ARG;
+  Cfg c;
+  PlanOut pl;
+  sk_status rc = plan_for_query(problems, count, cfg, cfg && cfg->num_ctas > 0 ? cfg->num_ctas : 0, &c, &pl);
+  if (rc != SK_OK) return rc;
+  *bytes = ws_bytes_for(c);
+  return SK_OK;
+}
+
+sk_status sk_workspace_init(void *ws, size_t ws_bytes, sk_stream_t stream) {
+  if (!ws || ws_bytes < 256) return SK_ERR_INVALID_ARG;
+  return cuda_err(cudaMemsetAsync(ws, 0, ws_bytes, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+sk_status sk_gemm(const sk_problem *problem, const sk_config *cfg, void *ws, size_t ws_bytes, sk_stream_t stream) {
+  return run(problem, 1, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), 1);
+}
+
+sk_status sk_gemm_grouped(const sk_problem *problems, int count, const sk_config *cfg, void *ws, size_t ws_bytes,
+                          sk_stream_t stream) {
+  return run(problems, count, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), MAXP_GROUPED);
+}
+
+sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc, void *dA, int64_t ldda, void *dB,
+                           int64_t lddb, const sk_config *cfg, void *ws, size_t ws_bytes, sk_stream_t stream) {
+  if (!fwd) return SK_ERR_INVALID_ARG;
+  if (fwd->a_type != SK_BF16 || fwd->b_type != SK_BF16 || fwd->c_type != SK_BF16) return SK_ERR_UNSUPPORTED;
+  if (fwd->m < 0 || fwd->n < 0 || fwd->k < 0) return SK_ERR_INVALID_ARG;
+  sk_problem pr[2];
+  int n = 0;
+  if (dA) {   // dA (m x k) = dC (m x n) * B^T (n x k)
+    sk_problem p;
+    std::memset(&p, 0, sizeof(p));
+    p.m = fwd->m;
+    p.n = fwd->k;
+    p.k = fwd->n;
+    p.a_type = p.b_type = SK_BF16;
+    p.c_type = fwd->a_type;
+    p.A = dC;
+    p.a_layout = SK_ROW_MAJOR;
+    p.lda = lddc;
+    p.B = fwd->B;
+    p.b_layout = flip(fwd->b_layout);
+    p.ldb = fwd->ldb;
+    p.C = dA;
+    p.c_layout = fwd->a_layout;
+    p.ldc = ldda;
+    p.alpha = 1.f;
+    p.beta = 0.f;
+    pr[n++] = p;
+  }
+  if (dB) {   // dB (k x n) = A^T (k x m) * dC (m x n)
+    sk_problem p;
+    std::memset(&p, 0, sizeof(p));
+    p.m = fwd->k;
+    p.n = fwd->n;
+    p.k = fwd->m;
+    p.a_type = p.b_type = SK_BF16;
+    p.c_type = fwd->b_type;
+    p.A = fwd->A;
+    p.a_layout = flip(fwd->a_layout);
+    p.lda = fwd->lda;
+    p.B = dC;
+    p.b_layout = SK_ROW_MAJOR;
+    p.ldb = lddc;
+    p.C = dB;
+    p.c_layout = fwd->b_layout;
+    p.ldc = lddb;
+    p.alpha = 1.f;
+    p.beta = 0.f;
+    pr[n++] = p;
+  }
+  if (n == 0) return SK_OK;
+  return run(pr, n, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), MAXP_GROUPED);
+}
+
+sk_status sk_quantize_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_out, float *amax_work,
+                           sk_stream_t stream) {
+  if (n < 0 || (n > 0 && (!x || !q)) || !scale_out || !amax_work) return SK_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(x) & 7u) || (reinterpret_cast<uintptr_t>(q) & 1u)) return SK_ERR_UNSUPPORTED;
+  return cuda_err(launch_quant_e4m3(x, n, q, scale_out, amax_work, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+sk_status sk_get_status(const void *ws, size_t ws_bytes, sk_stream_t stream, int clear, sk_status *device_status) {
+  if (!ws || ws_bytes < 256 || !device_status) return SK_ERR_INVALID_ARG;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SK_ERR_CUDA;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, ws, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SK_ERR_CUDA;
+  *device_status = v == 0 ? SK_OK : (sk_status)v;
+  if (clear && v != 0) {
+    if (cudaMemset(const_cast<void *>(ws), 0, sizeof(v)) != cudaSuccess) return SK_ERR_CUDA;
+  }
+  return SK_OK;
+}
+
+sk_status sk_plan_query(const sk_problem *problems, int count, const sk_config *cfg, int num_sms,
+                        sk_plan_info *out) {
+  if (!out) return SK_ERR_INVALID_ARG;
+  Cfg c;
+  PlanOut pl;
+  sk_status rc = plan_for_query(problems, count, cfg, num_sms, &c, &pl);
+  if (rc != SK_OK) return rc;
+  out->tile_m = c.BM;
+  out->tile_n = c.BN;
+  out->tile_k = c.BK;
+  out->stages = c.stages;
+  out->mode = c.mode;
+  out->num_ctas = c.g;
+  out->sk_units = pl.s.sk_units;
+  out->tiles = pl.s.total_tiles;
+  out->sk_tiles = pl.s.sk_tiles;
+  out->dp_tiles = pl.s.total_tiles - pl.s.sk_tiles;
+  out->sk_iters = pl.s.sk_iters;
+  out->iters_per_unit = pl.s.q;
+  out->extra_units = pl.s.r;
+  out->workspace_bytes = ws_bytes_for(c);
+  return SK_OK;
+}
+
+sk_status sk_plan_unit_items(const sk_problem *problems, int count, const sk_config *cfg, int num_sms, int unit,
+                             sk_work_item *items, int max_items, int *n_items) {
+  if (!n_items || max_items < 0 || (max_items > 0 && !items)) return SK_ERR_INVALID_ARG;
+  Cfg c;
+  PlanOut pl;
+  sk_status rc = plan_for_query(problems, count, cfg, num_sms, &c, &pl);
+  if (rc != SK_OK) return rc;
+  if (unit < 0 || unit >= c.g) return SK_ERR_INVALID_ARG;
+  Cursor cur;
+  cursor_init(pl.s, unit, cur);
+  Item w;
+  int n = 0;
+  while (pl.s.num_problems > 0 && cursor_next(pl.s, pl.ps.data(), unit, cur, w)) {
+    if (n < max_items) {
+      sk_work_item &o = items[n];
+      o.problem = pl.orig_index[w.problem];
+      o.tile = w.tile;
+      o.tile_row = w.tm;
+      o.tile_col = w.tn;
+      o.k0 = w.k0;
+      o.k1 = w.k1;
+      o.role = w.role;
+      o.peer_first = w.peer_first;
+      o.peer_last = w.peer_last;
+      o.pad = 0;
+      o.global_tile = w.gtile;
+    }
+    ++n;
+  }
+  *n_items = n;
+  return SK_OK;
+}
+
+}  // extern "C"

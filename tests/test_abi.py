@@ -1,0 +1,182 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point include/skgemm.h declares, rejects bad arguments before launching, and
+its host-side scheduler (the same code the kernels run) reproduces the
+oracle's schedule simulator exactly."""
+import ctypes
+import os
+import random
+import re
+
+import pytest
+
+from oracle import schedule as sch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sk():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2407_00044_gb300 as sk
+    return sk
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "skgemm.h")).read()
+    return sorted(set(re.findall(r"SK_API\s+[\w\s\*]+?\b(sk_\w+)\s*\(", txt)))
+
+
+def test_header_declares_expected_api():
+    syms = header_symbols()
+    for name in ("sk_gemm", "sk_gemm_grouped", "sk_gemm_backward", "sk_workspace_size",
+                 "sk_get_status", "sk_status_string"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(sk):
+    lib = ctypes.CDLL(sk.binding.LIB_PATH)
+    for name in header_symbols():
+        assert hasattr(lib, name), name
+    assert set(header_symbols()) == set(sk.binding.declared_symbols())
+
+
+def test_status_strings(sk):
+    B = sk.binding
+    assert B.sk_status_string(B.SK_OK) == "SK_OK"
+    assert B.sk_status_string(B.SK_ERR_TIMEOUT) == "SK_ERR_TIMEOUT"
+    assert B.sk_status_string(99) == "SK_ERR_UNKNOWN"
+
+
+def _q(sk, p, cfg=None, sms=148):
+    B = sk.binding
+    arr = (B.sk_problem * 1)(p)
+    info = B.sk_plan_info()
+    c = sk.api._cfg(cfg)
+    return B.sk_plan_query(arr, 1, ctypes.byref(c), sms, ctypes.byref(info)), info
+
+
+def test_argument_errors(sk):
+    B = sk.binding
+    p = sk.shape_problem(64, 64, 64)
+    assert _q(sk, p)[0] == B.SK_OK
+    bad = sk.shape_problem(64, 64, 64)
+    bad.m = -1
+    assert _q(sk, bad)[0] == B.SK_ERR_INVALID_ARG
+    bad = sk.shape_problem(64, 64, 64)
+    bad.lda = 10        # < K for row-major A
+    assert _q(sk, bad)[0] == B.SK_ERR_INVALID_ARG
+    bad = sk.shape_problem(64, 64, 64)
+    bad.b_type = B.SK_F32   # mixed input types
+    assert _q(sk, bad)[0] == B.SK_ERR_UNSUPPORTED
+    bad = sk.shape_problem(64, 64, 64)
+    bad.A = None
+    assert _q(sk, bad)[0] == B.SK_ERR_INVALID_ARG
+    bad = sk.shape_problem(64, 64, 64)
+    bad.beta = 1.0      # beta != 0 needs C_in
+    assert _q(sk, bad)[0] == B.SK_ERR_INVALID_ARG
+    assert _q(sk, p, {"tile_n": 96})[0] == B.SK_ERR_UNSUPPORTED
+    assert _q(sk, p, {"num_ctas": 149}, sms=148)[0] == B.SK_ERR_INVALID_ARG
+    assert _q(sk, p, {"stages": 9})[0] == B.SK_ERR_UNSUPPORTED
+    assert _q(sk, p, {"mode": 7})[0] == B.SK_ERR_INVALID_ARG
+    # m == 0: valid, nothing to do
+    z = sk.shape_problem(0, 64, 64)
+    assert _q(sk, z)[0] == B.SK_OK
+
+
+def test_workspace_size(sk):
+    B = sk.binding
+    p = sk.shape_problem(384, 384, 2048, dtype="f32")
+    n = ctypes.c_size_t(0)
+    c = sk.api._cfg({"num_ctas": 148})
+    assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+    assert n.value == 256 + 768 + 148 * 128 * 128 * 4
+    p = sk.shape_problem(384, 384, 2048)
+    assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+    assert n.value == 256 + 768 + 148 * 128 * 256 * 4
+
+
+def test_gemm_without_device_reports_no_device(sk):
+    """No GPU here: the call must fail cleanly, never fall back."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    B = sk.binding
+    p = sk.shape_problem(64, 64, 64)
+    c = sk.api._cfg(None)
+    assert B.sk_gemm(ctypes.byref(p), ctypes.byref(c), None, 0, None) == B.SK_ERR_NO_DEVICE
+
+
+def _lib_schedule(sk, problems_shapes, cfg, sms, dtype="bf16"):
+    probs = [sk.shape_problem(M, N, K, dtype=dtype) for (M, N, K) in problems_shapes]
+    B = sk.binding
+    arr = (B.sk_problem * len(probs))(*probs)
+    info = B.sk_plan_info()
+    c = sk.api._cfg(cfg)
+    assert B.sk_plan_query(arr, len(probs), ctypes.byref(c), sms, ctypes.byref(info)) == B.SK_OK
+    units = [sk.unit_items(probs, u, config=cfg, num_sms=sms) for u in range(info.num_ctas)]
+    return info, units
+
+
+_ROLE = {0: "whole", 1: "owner", 2: "peer", 3: "dp"}
+
+
+def _compare(sk, shapes, mode, sms, dtype="bf16", tile_n=0, min_ipu=1):
+    cfg = {"mode": mode, "tile_n": tile_n, "min_iters_per_unit": min_ipu}
+    info, units = _lib_schedule(sk, shapes, cfg, sms, dtype)
+    BM, BN, BK = info.tile_m, info.tile_n, info.tile_k
+    problems = []
+    for (M, N, K) in shapes:
+        tm, tn = sch.tile_grid(M, N, BM, BN)
+        problems.append((tm * tn, -(-K // BK)))
+    plan = sch.simulate(problems, sms, mode, min_iters_per_unit=min_ipu)
+    assert info.sk_tiles == plan.sk_tiles
+    assert info.sk_iters == plan.sk_iters
+    assert info.sk_units == plan.sk_units
+    assert info.tiles == len(plan.tiles)
+    for u in range(sms):
+        exp = [(s.tile, s.problem, s.local_tile, s.k0, s.k1, s.role,
+                (s.peers[0], s.peers[-1]) if s.role == "owner" else None)
+               for s in plan.units[u]]
+        got = [(w.global_tile, w.problem, w.tile, w.k0, w.k1, _ROLE[w.role],
+                (w.peer_first, w.peer_last) if w.role == 1 else None)
+               for w in units[u]]
+        assert got == exp, f"unit {u}"
+    # rasterisation is a bijection on every problem's tile grid
+    for p, (M, N, K) in enumerate(shapes):
+        tm_n, tn_n = sch.tile_grid(M, N, BM, BN)
+        coords = {}
+        for us in units:
+            for w in us:
+                if w.problem == p:
+                    assert 0 <= w.tile_row < tm_n and 0 <= w.tile_col < tn_n
+                    coords.setdefault(w.tile, set()).add((w.tile_row, w.tile_col))
+        flat = [c for s in coords.values() for c in s]
+        assert all(len(s) == 1 for s in coords.values())
+        assert len(set(flat)) == len(flat) == tm_n * tn_n
+
+
+@pytest.mark.parametrize("mode", sch.MODES)
+def test_host_scheduler_matches_simulator_sweep_shapes(sk, mode):
+    for shape in [(3840, 4096, 4096), (1536, 1536, 8192), (2048, 7168, 1024),
+                  (128, 8192, 16384), (1920, 2000, 2000), (480, 512, 512), (1, 1, 1)]:
+        _compare(sk, [shape], mode, 148)
+
+
+@pytest.mark.parametrize("mode", sch.MODES)
+def test_host_scheduler_matches_simulator_random(sk, mode):
+    rnd = random.Random(99)
+    for _ in range(40):
+        nprob = rnd.choice([1, 1, 2, 4, 9])
+        shapes = [(rnd.randint(1, 1500), rnd.randint(1, 1500), rnd.randint(1, 3000)) for _ in range(nprob)]
+        sms = rnd.randint(1, 152)
+        _compare(sk, shapes, mode, sms, dtype=rnd.choice(["bf16", "f32", "e4m3"]),
+                 min_ipu=rnd.choice([1, 1, 4]))
+
+
+def test_host_scheduler_unit_count_sweep(sk):
+    """The paper's 'compute unit' bug appeared for sub-maximal CU counts:
+    every g from 1 to 152 must give the simulator's exact schedule."""
+    for g in range(1, 153):
+        _compare(sk, [(384, 384, 2048)], "sk", g, dtype="f32")
+        _compare(sk, [(480, 512, 512)], "hybrid2", g)

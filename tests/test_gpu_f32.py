@@ -1,0 +1,128 @@
+"""GPU parity of the FP32 SIMT Stream-K path against the FP64 oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from gpu_common import assert_within_bound, dev, same_strides, sk, to_np
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["dp", "sk", "hybrid1", "hybrid2"]
+
+
+@pytest.fixture(scope="module")
+def m():
+    return sk()
+
+
+def _run(m, a, b, **kw):
+    d = dev()
+    cfg = kw.pop("config", None)
+    c = m.gemm(a.to(d), b.to(d), config=cfg, **kw)
+    assert m.default_workspace(d).status() == 0
+    return c
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_fp32_config1_modes(m, mode):
+    """384x384x2048, 128x128 tiles: 9 tiles < SMs, so SK splits every tile."""
+    cfg = workloads.FP32_SMALL
+    a, b = workloads.gemm_inputs(cfg["M"], cfg["N"], cfg["K"], dtype="f32", seed=0)
+    c = _run(m, a, b, config=m.Config(mode=mode))
+    assert_within_bound(c, a, b, what=f"fp32 {mode}")
+
+
+def test_fp32_small_int_exact(m):
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=1, dist="int")
+    ref, _ = oracle.gemm(a, b)
+    for mode in MODES:
+        c = _run(m, a, b, config=m.Config(mode=mode))
+        assert np.array_equal(to_np(c), ref), mode
+
+
+def test_fp32_unit_count_sweep(m):
+    """Every CTA count g, including the sub-maximal ones the paper's
+    Methodology/Results report as broken in the studied implementation."""
+    sms = torch.cuda.get_device_properties(dev()).multi_processor_count
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=2, dist="int")
+    ref, _ = oracle.gemm(a, b)
+    for g in sorted({1, 2, 3, 7, sms // 2, sms - 1, sms}):
+        for mode in ("sk", "hybrid2"):
+            c = _run(m, a, b, config=m.Config(mode=mode, num_ctas=g, min_iters_per_unit=1))
+            assert np.array_equal(to_np(c), ref), (g, mode)
+
+
+@pytest.mark.parametrize("al", ["row", "col"])
+@pytest.mark.parametrize("bl", ["row", "col"])
+@pytest.mark.parametrize("cl", ["row", "col"])
+def test_fp32_layouts_beta(m, al, bl, cl):
+    M, N, K = 130, 67, 93
+    a, b = workloads.gemm_inputs(M, N, K, dtype="f32", a_layout=al, b_layout=bl, seed=3)
+    c0 = workloads.as_layout(workloads.uniform((M, N), seed=4), cl)
+    d = dev()
+    ad, bd, c0d = same_strides(a, d), same_strides(b, d), same_strides(c0, d)
+    out = torch.empty_strided(c0.shape, c0.stride(), device=d)
+    m.gemm(ad, bd, out, alpha=0.75, beta=-1.5, C_in=c0d, config=m.Config(mode="sk"))
+    assert m.default_workspace(d).status() == 0
+    assert_within_bound(out, a, b, alpha=0.75, beta=-1.5, C0=c0, what=f"{al}{bl}{cl}")
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 127, 129), (129, 257, 33), (480, 512, 512), (5, 300, 4000)])
+def test_fp32_ragged(m, shape):
+    M, N, K = shape
+    a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=5)
+    for mode in ("sk", "dp"):
+        c = _run(m, a, b, config=m.Config(mode=mode, min_iters_per_unit=1))
+        assert_within_bound(c, a, b, what=f"{shape} {mode}")
+
+
+def test_fp32_deterministic_and_graph(m):
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=6)
+    d = dev()
+    ad, bd = a.to(d), b.to(d)
+    cfg = m.Config(mode="sk")
+    c1 = m.gemm(ad, bd, config=cfg)
+    c2 = m.gemm(ad, bd, config=cfg)
+    assert torch.equal(c1, c2)
+    out = torch.empty_like(c1)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        m.gemm(ad, bd, out, config=cfg)   # first call outside capture
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            m.gemm(ad, bd, out, config=cfg)
+    for _ in range(3):
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, c1)
+
+
+def test_fp32_k_zero(m):
+    d = dev()
+    a = torch.empty(5, 0, device=d)
+    b = torch.empty(0, 7, device=d)
+    c0 = workloads.uniform((5, 7), seed=7).to(d)
+    out = torch.full((5, 7), 3.0, device=d)
+    m.gemm(a, b, out, beta=2.0, C_in=c0)
+    assert torch.equal(out, 2.0 * c0)
+    m.gemm(a, b, out)
+    assert torch.equal(out, torch.zeros_like(out))
+
+
+def test_fp32_timeout_status_and_recovery(m):
+    """Peers withhold their flags (test-only injection): every owner's
+    bounded wait must expire, the kernel must return, the status word must
+    read SK_ERR_TIMEOUT, and the context must stay usable."""
+    d = dev()
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=8)
+    ad, bd = a.to(d), b.to(d)
+    ws = m.Workspace(d)
+    m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1), workspace=ws)
+    assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT
+    m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
+    c = m.gemm(ad, bd, config=m.Config(mode="sk"), workspace=ws)
+    assert ws.status() == 0
+    assert_within_bound(c, a, b, what="after timeout")
