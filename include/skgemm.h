@@ -214,6 +214,11 @@ SK_API sk_status sk_plan_unit_items(const sk_problem *problems, int count,
                              const sk_config *cfg, int num_sms, int unit,
                              sk_work_item *items, int max_items, int *n_items);
 
+/* Description of the last failure this thread saw inside the library
+ * (the CUDA call and its error string), or "" if none.  Static per-thread
+ * storage, valid until the thread's next call into the library. */
+SK_API const char *sk_last_error(void);
+
 /* Library version string. */
 SK_API const char *sk_version(void);
 

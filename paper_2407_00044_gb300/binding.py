@@ -91,6 +91,7 @@ _SIGNATURES = {
     "sk_plan_query": (_st, [_P(sk_problem), ctypes.c_int, _P(sk_config), ctypes.c_int, _P(sk_plan_info)]),
     "sk_plan_unit_items": (_st, [_P(sk_problem), ctypes.c_int, _P(sk_config), ctypes.c_int, ctypes.c_int,
                                  _P(sk_work_item), ctypes.c_int, _P(ctypes.c_int)]),
+    "sk_last_error": (ctypes.c_char_p, []),
     "sk_version": (ctypes.c_char_p, []),
 }
 
@@ -162,6 +163,10 @@ def sk_plan_unit_items(problems, count, cfg, num_sms, unit, items, max_items, n_
     return load().sk_plan_unit_items(problems, count, cfg, num_sms, unit, items, max_items, n_out)
 
 
+def sk_last_error() -> str:
+    return load().sk_last_error().decode()
+
+
 def sk_version() -> str:
     return load().sk_version().decode()
 
@@ -169,7 +174,8 @@ def sk_version() -> str:
 class SkError(RuntimeError):
     def __init__(self, status: int, where: str = ""):
         self.status = status
-        super().__init__(f"{where}: {sk_status_string(status)} ({status})")
+        detail = sk_last_error()
+        super().__init__(f"{where}: {sk_status_string(status)} ({status})" + (f" [{detail}]" if detail else ""))
 
 
 def check(status: int, where: str = ""):

@@ -233,6 +233,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
 
 template <int MAXP>
 cudaError_t launch_simt_f32(const SimtParams<MAXP> &p, int grid, cudaStream_t st) {
+  (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   sk_simt_f32_kernel<MAXP><<<grid, F32_THREADS, 0, st>>>(p);
   return cudaGetLastError();
 }

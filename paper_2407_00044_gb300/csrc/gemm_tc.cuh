@@ -416,6 +416,7 @@ template <int IN, typename OutT, int BN, int MAXP>
 cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
   auto kern = sk_tc_kernel<IN, OutT, BN, MAXP>;
   const int smem = tc_smem_bytes(BN, p.stages);
+  (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, 192, smem, st>>>(p);

@@ -6,8 +6,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "../../include/skgemm.h"
@@ -16,6 +18,21 @@
 using namespace sk;
 
 namespace {
+
+// Last failure seen by this thread (sk_last_error).
+thread_local std::string t_last_error;
+
+sk_status fail_cuda(const char *what, cudaError_t e) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+  t_last_error = buf;
+  return SK_ERR_CUDA;
+}
+
+sk_status fail_msg(sk_status s, const char *what) {
+  t_last_error = what;
+  return s;
+}
 
 // ------------------------------------------------------------------ device
 struct DevInfo {
@@ -56,7 +73,7 @@ sk_status encoder(EncodeTiledFn *fn) {
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
             cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !p)
-      return SK_ERR_CUDA;
+      return fail_msg(SK_ERR_CUDA, "cudaGetDriverEntryPointByVersion(cuTensorMapEncodeTiled) failed");
     g_encode = reinterpret_cast<EncodeTiledFn>(p);
   }
   *fn = g_encode;
@@ -295,7 +312,9 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 }
 
 // --------------------------------------------------------------- launches
-sk_status cuda_err(cudaError_t e) { return e == cudaSuccess ? SK_OK : SK_ERR_CUDA; }
+sk_status cuda_err(cudaError_t e, const char *what = "CUDA call") {
+  return e == cudaSuccess ? SK_OK : fail_cuda(what, e);
+}
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
@@ -327,7 +346,12 @@ sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk
   strides[0] = (cuuint64_t)ld * es;
   CUresult r = enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? SK_OK : SK_ERR_CUDA;
+  if (r != CUDA_SUCCESS) {
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), "cuTensorMapEncodeTiled failed (CUresult %d)", (int)r);
+    return fail_msg(SK_ERR_CUDA, buf);
+  }
+  return SK_OK;
 }
 
 template <int MAXP>
@@ -395,7 +419,7 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
     }
   }
   delete P;
-  return cuda_err(e);
+  return cuda_err(e, "tcgen05 GEMM launch");
 }
 
 template <int MAXP>
@@ -443,12 +467,13 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
   P->debug_flags = c.debug_flags;
   cudaError_t e = launch_simt_f32<MAXP>(*P, pl.grid, st);
   delete P;
-  return cuda_err(e);
+  return cuda_err(e, "FP32 GEMM launch");
 }
 
 // Shared driver of sk_gemm / sk_gemm_grouped / sk_gemm_backward.
 sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void *ws, size_t ws_bytes,
               cudaStream_t st, int maxp) {
+  t_last_error.clear();
   if (!problems || count < 1 || count > maxp) return SK_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     sk_status rc = check_problem(&problems[i]);
@@ -490,7 +515,7 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
     if (ws_bytes < ws_bytes_for(c)) return SK_ERR_WORKSPACE_TOO_SMALL;
   }
   for (const Norm &n : scale_only) {
-    rc = cuda_err(launch_scale(n.C, n.C_in, n.ldc, n.M, n.N, n.beta, n.c_type == SK_F32, st));
+    rc = cuda_err(launch_scale(n.C, n.C_in, n.ldc, n.M, n.N, n.beta, n.c_type == SK_F32, st), "k=0 scale launch");
     if (rc != SK_OK) return rc;
   }
   if (work.empty()) return SK_OK;
@@ -542,6 +567,8 @@ extern "C" {
 
 const char *sk_version(void) { return "skgemm 0.1 (sm_103a)"; }
 
+const char *sk_last_error(void) { return t_last_error.c_str(); }
+
 const char *sk_status_string(sk_status s) {
   switch (s) {
     case SK_OK: return "SK_OK";
@@ -567,7 +594,7 @@ sk_status sk_workspace_size(const sk_problem *problems, int count, const sk_conf
 
 sk_status sk_workspace_init(void *ws, size_t ws_bytes, sk_stream_t stream) {
   if (!ws || ws_bytes < 256) return SK_ERR_INVALID_ARG;
-  return cuda_err(cudaMemsetAsync(ws, 0, ws_bytes, reinterpret_cast<cudaStream_t>(stream)));
+  return cuda_err(cudaMemsetAsync(ws, 0, ws_bytes, reinterpret_cast<cudaStream_t>(stream)), "cudaMemsetAsync");
 }
 
 sk_status sk_gemm(const sk_problem *problem, const sk_config *cfg, void *ws, size_t ws_bytes, sk_stream_t stream) {
@@ -636,18 +663,22 @@ sk_status sk_quantize_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_o
                            sk_stream_t stream) {
   if (n < 0 || (n > 0 && (!x || !q)) || !scale_out || !amax_work) return SK_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(x) & 7u) || (reinterpret_cast<uintptr_t>(q) & 1u)) return SK_ERR_UNSUPPORTED;
-  return cuda_err(launch_quant_e4m3(x, n, q, scale_out, amax_work, reinterpret_cast<cudaStream_t>(stream)));
+  return cuda_err(launch_quant_e4m3(x, n, q, scale_out, amax_work, reinterpret_cast<cudaStream_t>(stream)),
+                  "E4M3 quantise launch");
 }
 
 sk_status sk_get_status(const void *ws, size_t ws_bytes, sk_stream_t stream, int clear, sk_status *device_status) {
   if (!ws || ws_bytes < 256 || !device_status) return SK_ERR_INVALID_ARG;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return SK_ERR_CUDA;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_cuda("cudaStreamSynchronize", e);
   uint32_t v = 0;
-  if (cudaMemcpy(&v, ws, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return SK_ERR_CUDA;
+  e = cudaMemcpy(&v, ws, sizeof(v), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return fail_cuda("cudaMemcpy(status)", e);
   *device_status = v == 0 ? SK_OK : (sk_status)v;
   if (clear && v != 0) {
-    if (cudaMemset(const_cast<void *>(ws), 0, sizeof(v)) != cudaSuccess) return SK_ERR_CUDA;
+    e = cudaMemset(const_cast<void *>(ws), 0, sizeof(v));
+    if (e != cudaSuccess) return fail_cuda("cudaMemset(status)", e);
   }
   return SK_OK;
 }

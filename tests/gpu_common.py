@@ -32,10 +32,11 @@ def assert_within_bound(got, A, B, *, alpha=1.0, beta=0.0, C0=None, out="f32", w
     """|got - ref| <= 5e-5 * S (+ 5e-5 |beta C0|) (+ 2^-8 |ref| for BF16
     output), element by element, with ref and S from the FP64 oracle on the
     same (already rounded) inputs."""
-    ref, S = oracle.gemm(A.cpu(), B.cpu(), alpha=alpha, beta=beta,
-                         C0=None if C0 is None else C0.cpu())
+    host = lambda x: x.cpu() if isinstance(x, torch.Tensor) else x   # noqa: E731
+    ref, S = oracle.gemm(host(A), host(B), alpha=alpha, beta=beta,
+                         C0=None if C0 is None else host(C0))
     g = to_np(got)
-    bc0 = None if (C0 is None or beta == 0.0) else beta * oracle.to_f64(C0.cpu())
+    bc0 = None if (C0 is None or beta == 0.0) else beta * oracle.to_f64(host(C0))
     tol = oracle.bound(S, ref, out, beta_c0=bc0)
     err = np.abs(g - ref)
     bad = ~(err <= tol)

@@ -101,7 +101,7 @@ def test_bf16_stages(m, stages):
 
 
 def test_bf16_beta(m):
-    M, N, K = 260, 530, 777
+    M, N, K = 260, 530, 776   # K * 2 bytes must be a multiple of 16 (TMA)
     a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=8)
     d = dev()
     c0 = workloads.uniform((M, N), seed=9).to(torch.bfloat16)
@@ -127,6 +127,17 @@ def test_bf16_transposed_layouts(m, al, bl, cl):
     assert m.default_workspace(d).status() == 0
     ref, _ = oracle.gemm(a, b)
     assert np.array_equal(to_np(out), ref), (al, bl, cl)
+
+
+def test_bf16_rejects_unaligned_leading_dimension(m):
+    """K = 777 BF16 elements is not a 16-byte row pitch: TMA cannot read it,
+    so the call must fail before launching anything."""
+    d = dev()
+    a = torch.zeros(64, 777, dtype=torch.bfloat16, device=d)
+    b = torch.zeros(777, 64, dtype=torch.bfloat16, device=d)
+    with pytest.raises(m.SkError) as e:
+        m.gemm(a, b)
+    assert e.value.status == m.binding.SK_ERR_UNSUPPORTED
 
 
 def test_bf16_deterministic(m):

@@ -95,6 +95,33 @@ def test_backward_layouts_exact(m, al, bl):
     assert np.all(np.abs(to_np(dB) - rB) <= 2 ** -8 * np.abs(rB))
 
 
+def test_backward_from_another_thread(m):
+    """The autograd engine calls backward from its own thread: the library
+    must work from a thread other than the one that first used it."""
+    import threading
+    M, N, K = 128, 256, 192
+    d = dev()
+    a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=56)
+    g = workloads.normal((M, N), seed=57).to(torch.bfloat16)
+    res = {}
+
+    def work():
+        try:
+            torch.cuda.set_device(d)
+            res["out"] = m.gemm_backward(a.to(d), b.to(d), g.to(d))
+            torch.cuda.synchronize()
+        except Exception as e:   # surfaced below
+            res["err"] = e
+
+    t = threading.Thread(target=work)
+    t.start()
+    t.join()
+    assert "err" not in res, res.get("err")
+    dA, dB = res["out"]
+    assert_within_bound(dA, g, b.t(), out="bf16", what="dA (thread)")
+    assert_within_bound(dB, a.t(), g, out="bf16", what="dB (thread)")
+
+
 def test_autograd_matches_oracle(m):
     M, N, K = 256, 384, 512
     d = dev()
