@@ -219,6 +219,35 @@ SK_API sk_status sk_plan_unit_items(const sk_problem *problems, int count,
  * storage, valid until the thread's next call into the library. */
 SK_API const char *sk_last_error(void);
 
+/* sk_gemm for callers that cannot allocate device memory.  (The paper has
+ * no counterpart; this is a library convenience.)
+ *
+ * Who needs it: code whose device memory is owned entirely by another
+ * allocator -- a framework's caching allocator or a pre-reserved memory
+ * pool -- must not call cudaMalloc (it may synchronise the device and can
+ * fail once the pool holds the memory), and plug-in style callers may have
+ * nowhere to keep a workspace between calls.  This call needs neither: the
+ * workspace is a fixed 12 MiB array inside the library, present on every
+ * GPU that loads it until the process exits.  The call itself allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * Same operands, config and result as sk_gemm, except that tile_n = 0
+ * selects 128 here (so every SM fits).  Limit: the plan's workspace must
+ * fit in 12 MiB -- 128x128 tiles on up to 191 CTAs, or 128x256 tiles on up
+ * to 95 CTAs; larger requests return SK_ERR_WORKSPACE_TOO_SMALL before
+ * anything is launched.
+ *
+ * All calls share the one array per GPU.  Each call first zeroes its status
+ * word and flags on `stream`, so calls ordered on the GPU are independent,
+ * but calls that overlap on the GPU (different streams, no ordering between
+ * them) race on the array and give undefined results.  The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current); make that first call before capturing any stream.
+ * Device-side status (timeouts) is not readable through sk_get_status for
+ * this call. */
+SK_API sk_status sk_gemm_static_ws(const sk_problem *problem, const sk_config *cfg,
+                                   sk_stream_t stream);
+
 /* Library version string. */
 SK_API const char *sk_version(void);
 
