@@ -488,6 +488,13 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   sk_status rc = current_device(&dev, &di);
   if (rc != SK_OK) return rc;
   if (!(di.major == 10 && di.minor == 3)) return SK_ERR_NO_DEVICE;   // built for sm_103a only
+  // Make the device's primary context current on this thread: the
+  // tensor-map encoder is a driver call and fails with "invalid context" on
+  // threads (e.g. the autograd engine's) that have not touched the driver.
+  {
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return fail_cuda("cudaSetDevice", e);
+  }
   Cfg c;
   rc = resolve_cfg(fam, cfg, di.sms, &c);
   if (rc != SK_OK) return rc;
