@@ -107,11 +107,17 @@ typedef struct {
 
 /* Launch configuration.  Zero in any field selects the default. */
 typedef struct {
-    int tile_m;              /* 128 (all kernels) */
-    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (default 256) */
+    int tile_m;              /* 128, or 256 = CTA-pair kernel (two CTAs of a cluster
+                                share one 256 x tile_n tile through tcgen05
+                                cta_group::2; BF16/E4M3 with A row-major and B
+                                column-major only); 0 = automatic (256 when every
+                                problem allows it and has m >= 256) */
+    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (default 256; pair: 256) */
     int stages;              /* smem pipeline depth (BF16/E4M3: 2..6; default by tile) */
     sk_mode mode;            /* decomposition; default AUTO */
-    int num_ctas;            /* persistent CTAs g, 1 <= g <= SM count; 0 = SM count */
+    int num_ctas;            /* persistent CTAs, 1 <= num_ctas <= SM count; 0 = SM count.
+                                The pair kernel uses num_ctas / 2 pairs, at most as
+                                many as the GPU can hold at once */
     int min_iters_per_unit;  /* fewest k-blocks per Stream-K unit; default 4 */
     uint64_t timeout_ns;     /* bound on every device-side wait; default 2e9 ns */
     int debug_flags;         /* test-only fault injection, 0 in normal use:
@@ -123,8 +129,8 @@ typedef struct {
 typedef struct {
     int tile_m, tile_n, tile_k, stages;
     sk_mode mode;            /* never AUTO */
-    int num_ctas;            /* g */
-    int sk_units;            /* CTAs that take Stream-K iterations */
+    int num_ctas;            /* scheduler units g: CTAs, or CTA pairs if tile_m == 256 */
+    int sk_units;            /* units that take Stream-K iterations */
     int64_t tiles;           /* output tiles over all problems */
     int64_t sk_tiles;        /* leading tiles computed Stream-K */
     int64_t dp_tiles;        /* tiles computed whole, round-robin */

@@ -260,8 +260,10 @@ def shape_problem(M: int, N: int, K: int, dtype: str = "bf16", out: str | None =
     p.a_layout = B.SK_ROW_MAJOR if a_layout == "row" else B.SK_COL_MAJOR
     p.b_layout = B.SK_ROW_MAJOR if b_layout == "row" else B.SK_COL_MAJOR
     p.c_layout = B.SK_ROW_MAJOR
-    p.lda = max(1, K if a_layout == "row" else M)
-    p.ldb = max(1, N if b_layout == "row" else K)
+    # leading dimensions padded to 16 elements: legal TMA row pitches
+    pad = lambda x: -(-max(1, x) // 16) * 16   # noqa: E731
+    p.lda = pad(K if a_layout == "row" else M)
+    p.ldb = pad(N if b_layout == "row" else K)
     p.ldc = max(1, N)
     p.A = p.B = p.C = 16   # non-null placeholders; plan queries never dereference
     p.alpha, p.beta = 1.0, 0.0

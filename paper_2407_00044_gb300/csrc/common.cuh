@@ -89,8 +89,11 @@ inline int tc_smem_bytes(int bn, int stages) {
 template <int MAXP>
 cudaError_t launch_simt_f32(const SimtParams<MAXP> &p, int grid, cudaStream_t st);
 
-template <int IN, typename OutT, int BN, int MAXP>
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
 cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st);
+
+template <int IN, typename OutT, int BN, int MAXP>
+int pair_max_clusters(int stages);
 
 cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N,
                          float beta, int c_is_f32, cudaStream_t st);

@@ -3,10 +3,12 @@
 #include "gemm_tc.cuh"
 
 namespace sk {
-template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP_GROUPED>(const TcParams<MAXP_GROUPED> &, int,
-                                                                         cudaStream_t);
-template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP_GROUPED>(const TcParams<MAXP_GROUPED> &, int,
-                                                                         cudaStream_t);
-template cudaError_t launch_tc<IN_BF16, float, 256, MAXP_GROUPED>(const TcParams<MAXP_GROUPED> &, int, cudaStream_t);
-template cudaError_t launch_tc<IN_BF16, float, 128, MAXP_GROUPED>(const TcParams<MAXP_GROUPED> &, int, cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP_GROUPED, false>(const TcParams<MAXP_GROUPED> &, int,
+                                                                                cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP_GROUPED, false>(const TcParams<MAXP_GROUPED> &, int,
+                                                                                cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, float, 256, MAXP_GROUPED, false>(const TcParams<MAXP_GROUPED> &, int,
+                                                                        cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, float, 128, MAXP_GROUPED, false>(const TcParams<MAXP_GROUPED> &, int,
+                                                                        cudaStream_t);
 }  // namespace sk

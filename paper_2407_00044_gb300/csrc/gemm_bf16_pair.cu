@@ -1,0 +1,15 @@
+// BF16-input instantiations of the CTA-pair (256-row tile) Stream-K kernel.
+#include "gemm_tc.cuh"
+
+namespace sk {
+template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 256, 1, true>(const TcParams<1> &, int, cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, float, 256, 1, true>(const TcParams<1> &, int, cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP_GROUPED, true>(const TcParams<MAXP_GROUPED> &, int,
+                                                                               cudaStream_t);
+template cudaError_t launch_tc<IN_BF16, float, 256, MAXP_GROUPED, true>(const TcParams<MAXP_GROUPED> &, int,
+                                                                       cudaStream_t);
+template int pair_max_clusters<IN_BF16, __nv_bfloat16, 256, 1>(int);
+template int pair_max_clusters<IN_BF16, float, 256, 1>(int);
+template int pair_max_clusters<IN_BF16, __nv_bfloat16, 256, MAXP_GROUPED>(int);
+template int pair_max_clusters<IN_BF16, float, 256, MAXP_GROUPED>(int);
+}  // namespace sk

@@ -116,19 +116,32 @@ struct OutStore<__nv_bfloat16> {
   }
 };
 
-template <int IN, typename OutT, int BN, int MAXP>
+// PAIR = false: one CTA per unit, 128 x BN tile, tcgen05 cta_group::1.
+// PAIR = true : a cluster of two CTAs per unit, 256 x BN tile.  Each CTA
+//   TMA-loads its own 128 rows of A and its half (BN/2 rows) of B into its
+//   own shared memory; both loads complete on the leader CTA's `full`
+//   barrier; the leader's MMA warp issues tcgen05.mma.cta_group::2 (M=256),
+//   which reads both CTAs' operands and writes rows 0-127 of the tile into
+//   the leader's TMEM and rows 128-255 into the peer's; its commits arrive
+//   on both CTAs' barriers (multicast).  Each CTA's epilogue handles its own
+//   128 rows; both CTAs' epilogues release the leader's `tmem_empty`.  Each
+//   CTA of a pair has its own partial slot and flag (index 2*unit + rank).
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
 __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ TcParams<MAXP> P) {
   using Tr = InTraits<IN>;
-  constexpr int BM = 128;
+  constexpr int BM = PAIR ? 256 : 128;          // tile rows per unit
   constexpr int BK = Tr::BK;
   constexpr int UMMA_K = Tr::UMMA_K;
-  constexpr int A_BYTES = BM * 128;
-  constexpr int B_BYTES = BN * 128;
+  constexpr int B_ROWS = PAIR ? BN / 2 : BN;    // rows of B (N direction) this CTA loads
+  constexpr int A_BYTES = 128 * 128;
+  constexpr int B_BYTES = B_ROWS * 128;
   constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  constexpr int TX_BYTES = PAIR ? 2 * STAGE_BYTES : STAGE_BYTES;   // landing on the leader's barrier
   constexpr uint32_t TMEM_COLS = 2 * BN;
   constexpr int MN_CHUNK_BYTES = BK * 128;   // one 64-wide MN chunk of an MN-major slice
   constexpr uint32_t IDESC = Tr::IDESC_TYPES | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "tile N");
+  static_assert(!PAIR || BN % 64 == 0, "pair tile N");
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -146,7 +159,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int u = blockIdx.x;
+  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
+  const int u = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int slot_id = PAIR ? 2 * u + (int)rank : u;   // workspace slot / flag of this CTA
   const Sched &S = P.sched;
   const uint64_t tmo = P.timeout_ns;
 
@@ -157,7 +173,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(tfull_bar + a), 1);
-      mbar_init(smem_u32(tempty_bar + a), 4);
+      mbar_init(smem_u32(tempty_bar + a), PAIR ? 8 : 4);
     }
     mbar_init(smem_u32(done_bar), 1);
     *abort_flag = 0;
@@ -165,11 +181,17 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     fence_proxy_async_smem();
   }
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
-    tmem_relinquish();
+    if constexpr (PAIR) {
+      tmem_alloc_pair(smem_u32(tmem_slot), TMEM_COLS);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), TMEM_COLS);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (PAIR) cluster_sync();   // the peer's barriers exist before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -195,28 +217,37 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       bool ok = true;
       while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
         const TcProblem &pr = P.prob[w.problem];
-        const int m0 = w.tm * BM, n0 = w.tn * BN;
+        const int m0 = w.tm * BM + (int)rank * 128;
+        const int n0 = w.tn * BN + (int)rank * B_ROWS;
         for (int kb = w.k0; kb < w.k1; ++kb) {
           if (!mbar_wait(smem_u32(empty_bar + stage), phase ^ 1u, tmo) || *abort_flag) {
             ok = false;
             break;
           }
           const uint32_t fb = smem_u32(full_bar + stage);
-          mbar_arrive_expect_tx(fb, STAGE_BYTES);
+          if (leader) mbar_arrive_expect_tx(fb, TX_BYTES);
           const uint32_t sa = tiles_addr + stage * STAGE_BYTES;
           const uint32_t sb = sa + A_BYTES;
           const int kx = kb * BK;
-          if (!pr.a_mn) {
-            tma_load_2d(sa, &pr.tmap_a, fb, kx, m0);
+          if constexpr (PAIR) {
+            const uint32_t fbl = mapa_shared(fb, 0);   // the leader's barrier
+            tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
+            tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
           } else {
+            if (!pr.a_mn) {
+              tma_load_2d(sa, &pr.tmap_a, fb, kx, m0);
+            } else {
 #pragma unroll
-            for (int ch = 0; ch < BM / 64; ++ch) tma_load_2d(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fb, m0 + 64 * ch, kx);
-          }
-          if (!pr.b_mn) {
-            tma_load_2d(sb, &pr.tmap_b, fb, kx, n0);
-          } else {
+              for (int ch = 0; ch < 128 / 64; ++ch)
+                tma_load_2d(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fb, m0 + 64 * ch, kx);
+            }
+            if (!pr.b_mn) {
+              tma_load_2d(sb, &pr.tmap_b, fb, kx, n0);
+            } else {
 #pragma unroll
-            for (int ch = 0; ch < BN / 64; ++ch) tma_load_2d(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fb, n0 + 64 * ch, kx);
+              for (int ch = 0; ch < BN / 64; ++ch)
+                tma_load_2d(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fb, n0 + 64 * ch, kx);
+            }
           }
           ++loads;
           if (++stage == stages) {
@@ -228,13 +259,16 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       if (!ok) fail();
       // Drain (bounded): every issued TMA load must land before the CTA may
       // exit -- slot s last completed phase `phase` if s < stage, else the
-      // phase before -- and, on the normal path, every slot must have been
-      // released by the MMA warp's commits.
-      for (int s = 0; s < stages && s < loads; ++s) {
-        const uint32_t par = s < stage ? phase : (phase ^ 1u);
-        if (!mbar_wait(smem_u32(full_bar + s), par, tmo)) {
-          fail();
-          break;
+      // phase before (in a pair, the leader's barrier sees both CTAs'
+      // loads) -- and, on the normal path, every slot must have been
+      // released by the MMA's commits.
+      if (leader) {
+        for (int s = 0; s < stages && s < loads; ++s) {
+          const uint32_t par = s < stage ? phase : (phase ^ 1u);
+          if (!mbar_wait(smem_u32(full_bar + s), par, tmo)) {
+            fail();
+            break;
+          }
         }
       }
       for (int i = 0; i < stages && !*abort_flag; ++i) {
@@ -250,7 +284,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------- MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       int stage = 0;
       uint32_t phase = 0;
       int acc = 0;
@@ -262,7 +296,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
         const TcProblem &pr = P.prob[w.problem];
         const uint32_t idesc = IDESC | ((uint32_t)pr.a_mn << 15) | ((uint32_t)pr.b_mn << 16);
-        if (!mbar_wait(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo)) {
+        const bool got = PAIR ? mbar_wait_cluster(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo)
+                              : mbar_wait(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo);
+        if (!got) {
           ok = false;
           break;
         }
@@ -285,19 +321,32 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             const uint64_t bd = pr.b_mn ? smem_desc_sw128(sb + kk * UMMA_K * 128, MN_CHUNK_BYTES, 1024)
                                         : smem_desc_sw128(sb + kk * 32, 16, 1024);
             const uint32_t accum = (kb > w.k0 || kk > 0) ? 1u : 0u;
-            if constexpr (IN == IN_BF16)
-              mma_f16(d_tmem, ad, bd, idesc, accum);
-            else
-              mma_f8(d_tmem, ad, bd, idesc, accum);
+            if constexpr (PAIR) {
+              if constexpr (IN == IN_BF16)
+                mma_f16_pair(d_tmem, ad, bd, idesc, accum);
+              else
+                mma_f8_pair(d_tmem, ad, bd, idesc, accum);
+            } else {
+              if constexpr (IN == IN_BF16)
+                mma_f16(d_tmem, ad, bd, idesc, accum);
+              else
+                mma_f8(d_tmem, ad, bd, idesc, accum);
+            }
           }
-          mma_commit(smem_u32(empty_bar + stage));
+          if constexpr (PAIR)
+            mma_commit_pair_mc(smem_u32(empty_bar + stage), (uint16_t)3);
+          else
+            mma_commit(smem_u32(empty_bar + stage));
           if (++stage == stages) {
             stage = 0;
             phase ^= 1u;
           }
         }
         if (!ok) break;
-        mma_commit(smem_u32(tfull_bar + acc));
+        if constexpr (PAIR)
+          mma_commit_pair_mc(smem_u32(tfull_bar + acc), (uint16_t)3);
+        else
+          mma_commit(smem_u32(tfull_bar + acc));
         if (++acc == 2) {
           acc = 0;
           acc_phase ^= 1u;
@@ -305,7 +354,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       }
       if (!ok) fail();
       // All MMAs issued by this thread are complete once done_bar flips.
-      mma_commit(smem_u32(done_bar));
+      if constexpr (PAIR)
+        mma_commit_pair_mc(smem_u32(done_bar), (uint16_t)1);
+      else
+        mma_commit(smem_u32(done_bar));
       if (!mbar_wait(smem_u32(done_bar), 0u, tmo)) fail();
     }
   } else {
@@ -314,12 +366,23 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     const int row = q4 * 32 + lane;          // accumulator row of this thread
     const int et = threadIdx.x - 64;         // 0..127
     float4 *slots = reinterpret_cast<float4 *>(P.ws.partials);
-    constexpr int64_t SLOT_F4 = (int64_t)BM * BN / 4;
+    constexpr int64_t SLOT_F4 = (int64_t)128 * BN / 4;
     int acc = 0;
     uint32_t acc_phase = 0;
     Cursor c;
     cursor_init(S, u, c);
     Item w;
+    // Releases accumulator `a` to the MMA issuer (the leader's barrier).
+    auto release_acc = [&](int a) {
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if constexpr (PAIR)
+          mbar_arrive_cluster(mapa_shared(smem_u32(tempty_bar + a), 0));
+        else
+          mbar_arrive(smem_u32(tempty_bar + a));
+      }
+    };
     while (!*abort_flag && cursor_next(S, P.ps, u, c, w)) {
       const TcProblem &pr = P.prob[w.problem];
       if (!mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo)) {
@@ -330,7 +393,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       const uint32_t tbase = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN);
 
       if (w.role == ROLE_PEER) {
-        float4 *slot = slots + (int64_t)u * SLOT_F4;
+        float4 *slot = slots + (int64_t)slot_id * SLOT_F4;
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32];
@@ -339,19 +402,20 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           for (int j = 0; j < 8; ++j)
             __stcg(slot + (ch * 8 + j) * 128 + row, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(tempty_bar + acc));
+        release_acc(acc);
         __threadfence();
         named_bar_sync(1, 128);
-        if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + u, 1u);
+        if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + slot_id, 1u);
       } else {
+        // Peer units p hold their partial of this CTA's rows in slot
+        // (PAIR ? 2p + rank : p).
         if (w.role == ROLE_OWNER) {
           if (et == 0) {
             const uint64_t t0 = globaltimer();
             bool to = false;
             for (int p = w.peer_first; p <= w.peer_last && !to; ++p) {
-              while (ld_acquire_gpu(P.ws.flags + p) == 0u) {
+              const int ps = PAIR ? 2 * p + (int)rank : p;
+              while (ld_acquire_gpu(P.ws.flags + ps) == 0u) {
                 if (globaltimer() - t0 > tmo) {
                   atomicExch(P.ws.status, STATUS_TIMEOUT);
                   to = true;
@@ -367,15 +431,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           if (pr.scale_a) alpha *= *pr.scale_a;
           if (pr.scale_b) alpha *= *pr.scale_b;
         }
-        const int grow = w.tm * BM + row;
+        const int grow = w.tm * BM + (int)rank * 128 + row;
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32];
           tmem_ld32(tbase + ch * 32, v);
           if (w.role == ROLE_OWNER) {
-            // Fixed order: own accumulator, then peers in ascending CTA index.
+            // Fixed order: own accumulator, then peers in ascending unit index.
             for (int p = w.peer_first; p <= w.peer_last; ++p) {
-              const float4 *slot = slots + (int64_t)p * SLOT_F4;
+              const float4 *slot = slots + (int64_t)(PAIR ? 2 * p + (int)rank : p) * SLOT_F4;
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
                 float4 q = __ldcg(slot + (ch * 8 + j) * 128 + row);
@@ -391,11 +455,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(tempty_bar + acc));
+        release_acc(acc);
         if (w.role == ROLE_OWNER && et == 0)
-          for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[p] = 0u;
+          for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[PAIR ? 2 * p + (int)rank : p] = 0u;
       }
       if (++acc == 2) {
         acc = 0;
@@ -406,21 +468,70 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 
   tc_fence_before();
   __syncthreads();
+  // A pair's leader MMAs read the peer's shared memory and write its TMEM:
+  // neither CTA frees TMEM or exits before both are done.
+  if constexpr (PAIR) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    if constexpr (PAIR)
+      tmem_dealloc_pair(tmem_base, TMEM_COLS);
+    else
+      tmem_dealloc(tmem_base, TMEM_COLS);
   }
 }
 
-template <int IN, typename OutT, int BN, int MAXP>
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
 cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP>;
-  const int smem = tc_smem_bytes(BN, p.stages);
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR>;
+  const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages);
   (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 192, smem, st>>>(p);
-  return cudaGetLastError();
+  if constexpr (!PAIR) {
+    kern<<<grid, 192, smem, st>>>(p);
+    return cudaGetLastError();
+  } else {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0);
+    (void)e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(192, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, p);
+  }
+}
+
+// Co-resident clusters of two for the pair kernel (0 if it cannot launch).
+template <int IN, typename OutT, int BN, int MAXP>
+int pair_max_clusters(int stages) {
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, true>;
+  const int smem = tc_smem_bytes(BN / 2, stages);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(2, 1, 1);
+  cfg.blockDim = dim3(192, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 }  // namespace sk

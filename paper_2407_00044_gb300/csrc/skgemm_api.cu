@@ -183,11 +183,13 @@ Norm normalise(const sk_problem &p) {
 struct Cfg {
   Family fam;
   int BM, BN, BK, stages;
+  bool pair;       // CTA-pair kernel: a unit is a cluster of 2 CTAs, tile 256 x BN
   sk_mode mode;
-  int g;
+  int g;           // scheduler units (CTAs, or CTA pairs)
   int min_ipu;
   uint64_t timeout_ns;
   int debug_flags;
+  int ctas() const { return pair ? 2 * g : g; }
 };
 
 sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
@@ -196,9 +198,11 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   if (c) d = *c;
   Cfg r;
   r.fam = fam;
-  if (d.tile_m != 0 && d.tile_m != 128) return SK_ERR_UNSUPPORTED;
-  r.BM = 128;
+  if (d.tile_m != 128 && d.tile_m != 256) return SK_ERR_UNSUPPORTED;   // 0 was resolved by auto_tile
+  r.pair = d.tile_m == 256;
+  r.BM = d.tile_m;
   if (fam == FAM_F32) {
+    if (r.pair) return SK_ERR_UNSUPPORTED;
     if (d.tile_n != 0 && d.tile_n != 128) return SK_ERR_UNSUPPORTED;
     r.BN = 128;
     r.BK = F32_BK;
@@ -207,8 +211,9 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   } else {
     r.BN = d.tile_n ? d.tile_n : 256;
     if (r.BN != 128 && r.BN != 256) return SK_ERR_UNSUPPORTED;
+    if (r.pair && r.BN != 256) return SK_ERR_UNSUPPORTED;
     r.BK = fam == FAM_BF16 ? 64 : 128;
-    const int stage_bytes = 128 * 128 + r.BN * 128;
+    const int stage_bytes = 128 * 128 + (r.pair ? r.BN / 2 : r.BN) * 128;   // per CTA
     const int max_stages = std::min(6, (227 * 1024 - 1024 - 256) / stage_bytes);
     r.stages = d.stages ? d.stages : max_stages;
     if (r.stages < 2 || r.stages > max_stages) return SK_ERR_UNSUPPORTED;
@@ -217,7 +222,9 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.mode = d.mode == SK_MODE_AUTO ? SK_MODE_HYBRID2 : d.mode;
   if (sms <= 0) return SK_ERR_INVALID_ARG;
   if (d.num_ctas < 0 || d.num_ctas > sms) return SK_ERR_INVALID_ARG;
-  r.g = d.num_ctas ? d.num_ctas : sms;
+  const int ctas = d.num_ctas ? d.num_ctas : sms;
+  r.g = r.pair ? ctas / 2 : ctas;
+  if (r.g < 1) return SK_ERR_INVALID_ARG;
   if (d.min_iters_per_unit < 0) return SK_ERR_INVALID_ARG;
   r.min_ipu = d.min_iters_per_unit ? d.min_iters_per_unit : 4;
   r.timeout_ns = d.timeout_ns ? d.timeout_ns : 2000000000ull;
@@ -226,9 +233,10 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   return SK_OK;
 }
 
+// One partial slot (128 rows x BN FP32) and one flag per CTA.
 size_t ws_bytes_for(const Cfg &c) {
-  const size_t flags = ((size_t)c.g * 4 + 255) / 256 * 256;
-  return 256 + flags + (size_t)c.g * c.BM * c.BN * 4;
+  const size_t flags = ((size_t)c.ctas() * 4 + 255) / 256 * 256;
+  return 256 + flags + (size_t)c.ctas() * 128 * c.BN * 4;
 }
 
 Workspace carve(void *ws, const Cfg &c) {
@@ -236,9 +244,21 @@ Workspace carve(void *ws, const Cfg &c) {
   Workspace w;
   w.status = reinterpret_cast<uint32_t *>(b);
   w.flags = reinterpret_cast<uint32_t *>(b + 256);
-  const size_t flags = ((size_t)c.g * 4 + 255) / 256 * 256;
+  const size_t flags = ((size_t)c.ctas() * 4 + 255) / 256 * 256;
   w.partials = reinterpret_cast<float *>(b + 256 + flags);
   return w;
+}
+
+// Default tile when the caller leaves tile_m = 0: the CTA-pair kernel
+// (256-row tiles, half the per-SM operand traffic) when every problem has
+// K-major operands and at least 256 rows; otherwise 128-row tiles.
+int auto_tile_m(Family fam, const std::vector<Norm> &work) {
+  if (fam == FAM_F32 || work.empty()) return 128;
+  for (const Norm &n : work) {
+    if (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR) return 128;
+    if (n.M < 256) return 128;
+  }
+  return 256;
 }
 
 // -------------------------------------------------------------------- plan
@@ -308,7 +328,8 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
     s.r = 0;
   }
   const int64_t dp = tiles - s.sk_tiles;
-  out->grid = (int)std::max<int64_t>(s.sk_units, std::min<int64_t>(c.g, dp));
+  const int64_t units = std::max<int64_t>(s.sk_units, std::min<int64_t>(c.g, dp));
+  out->grid = (int)(c.pair ? 2 * units : units);
 }
 
 // --------------------------------------------------------------- launches
@@ -324,6 +345,10 @@ sk_status check_tc_alignment(const Norm &n) {
   if ((n.lda * es) % 16 != 0 || (n.ldb * es) % 16 != 0) return SK_ERR_UNSUPPORTED;
   if (n.in_type == SK_E4M3 && (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR)) return SK_ERR_UNSUPPORTED;
   return SK_OK;
+}
+
+sk_status check_pair_layout(const Norm &n) {
+  return (n.a_layout == SK_ROW_MAJOR && n.b_layout == SK_COL_MAJOR) ? SK_OK : SK_ERR_UNSUPPORTED;
 }
 
 sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk_dtype t, bool kmajor, int64_t rows,
@@ -370,7 +395,8 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
     const bool a_k = n.a_layout == SK_ROW_MAJOR;   // A(i,k) at A[i*lda + k]
     const bool b_k = n.b_layout == SK_COL_MAJOR;   // B(k,j) at B[k + j*ldb]
     rc = encode_operand(enc, &tp.tmap_a, n.A, n.in_type, a_k, n.M, n.K, n.lda, 128, c.BK);
-    if (rc == SK_OK) rc = encode_operand(enc, &tp.tmap_b, n.B, n.in_type, b_k, n.N, n.K, n.ldb, c.BN, c.BK);
+    if (rc == SK_OK)
+      rc = encode_operand(enc, &tp.tmap_b, n.B, n.in_type, b_k, n.N, n.K, n.ldb, c.pair ? c.BN / 2 : c.BN, c.BK);
     if (rc != SK_OK) {
       delete P;
       return rc;
@@ -399,20 +425,26 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
   if (c.fam == FAM_BF16) {
-    if (c.BN == 256)
-      e = f32out ? launch_tc<IN_BF16, float, 256, MAXP>(*P, pl.grid, st)
-                 : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP>(*P, pl.grid, st);
+    if (c.pair)
+      e = f32out ? launch_tc<IN_BF16, float, 256, MAXP, true>(*P, pl.grid, st)
+                 : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP, true>(*P, pl.grid, st);
+    else if (c.BN == 256)
+      e = f32out ? launch_tc<IN_BF16, float, 256, MAXP, false>(*P, pl.grid, st)
+                 : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP, false>(*P, pl.grid, st);
     else
-      e = f32out ? launch_tc<IN_BF16, float, 128, MAXP>(*P, pl.grid, st)
-                 : launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP>(*P, pl.grid, st);
+      e = f32out ? launch_tc<IN_BF16, float, 128, MAXP, false>(*P, pl.grid, st)
+                 : launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP, false>(*P, pl.grid, st);
   } else if (c.fam == FAM_E4M3) {
     if constexpr (MAXP == 1) {
-      if (c.BN == 256)
-        e = f32out ? launch_tc<IN_E4M3, float, 256, 1>(*P, pl.grid, st)
-                   : launch_tc<IN_E4M3, __nv_bfloat16, 256, 1>(*P, pl.grid, st);
+      if (c.pair)
+        e = f32out ? launch_tc<IN_E4M3, float, 256, 1, true>(*P, pl.grid, st)
+                   : launch_tc<IN_E4M3, __nv_bfloat16, 256, 1, true>(*P, pl.grid, st);
+      else if (c.BN == 256)
+        e = f32out ? launch_tc<IN_E4M3, float, 256, 1, false>(*P, pl.grid, st)
+                   : launch_tc<IN_E4M3, __nv_bfloat16, 256, 1, false>(*P, pl.grid, st);
       else
-        e = f32out ? launch_tc<IN_E4M3, float, 128, 1>(*P, pl.grid, st)
-                   : launch_tc<IN_E4M3, __nv_bfloat16, 128, 1>(*P, pl.grid, st);
+        e = f32out ? launch_tc<IN_E4M3, float, 128, 1, false>(*P, pl.grid, st)
+                   : launch_tc<IN_E4M3, __nv_bfloat16, 128, 1, false>(*P, pl.grid, st);
     } else {
       delete P;
       return SK_ERR_UNSUPPORTED;
@@ -470,10 +502,11 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
   return cuda_err(e, "FP32 GEMM launch");
 }
 
-// Shared driver of sk_gemm / sk_gemm_grouped / sk_gemm_backward.
-sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void *ws, size_t ws_bytes,
-              cudaStream_t st, int maxp) {
-  t_last_error.clear();
+// Normalises the problems, picks the tile (tile_m = 0: auto) and resolves
+// the config.  `work` gets the problems with m, n, k >= 1; `scale_only` the
+// ones with k == 0 (C = beta * C_in).
+sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, int sms, int maxp, Cfg *c,
+                  std::vector<Norm> *work, std::vector<int> *idx, std::vector<Norm> *scale_only) {
   if (!problems || count < 1 || count > maxp) return SK_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     sk_status rc = check_problem(&problems[i]);
@@ -483,6 +516,73 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   for (int i = 1; i < count; ++i)
     if (problems[i].a_type != problems[0].a_type || problems[i].c_type != problems[0].c_type)
       return SK_ERR_UNSUPPORTED;
+  for (int i = 0; i < count; ++i) {
+    const sk_problem &p = problems[i];
+    if (p.m == 0 || p.n == 0) continue;
+    Norm n = normalise(p);
+    if (p.k == 0) {
+      if (scale_only) scale_only->push_back(n);
+      continue;
+    }
+    work->push_back(n);
+    idx->push_back(i);
+  }
+  sk_config d;
+  std::memset(&d, 0, sizeof(d));
+  if (cfg) d = *cfg;
+  if (d.tile_m == 0) {
+    d.tile_m = auto_tile_m(fam, *work);
+    const int ctas = d.num_ctas > 0 ? d.num_ctas : sms;
+    if (ctas < 2) d.tile_m = 128;          // a pair needs two CTAs
+    if (d.tile_n == 128) d.tile_m = 128;   // pairs only come with 256-wide tiles
+  }
+  sk_status rc = resolve_cfg(fam, &d, sms, c);
+  if (rc != SK_OK) return rc;
+  for (const Norm &n : *work) {
+    if (fam != FAM_F32) {
+      rc = check_tc_alignment(n);
+      if (rc != SK_OK) return rc;
+    }
+    if (c->pair) {
+      rc = check_pair_layout(n);
+      if (rc != SK_OK) return rc;
+    }
+  }
+  return SK_OK;
+}
+
+// Co-resident CTA pairs of the pair kernel that this call would launch
+// (cached per device and variant).
+int pair_clusters(int dev, const Cfg &c, bool f32out, bool grouped) {
+  static std::mutex mu;
+  static int cache[64][2][2][2][8] = {};
+  const int fi = c.fam == FAM_E4M3 ? 1 : 0;
+  const int st = c.stages & 7;
+  std::lock_guard<std::mutex> lk(mu);
+  int &slot = cache[dev][fi][f32out][grouped][st];
+  if (slot == 0) {
+    int n = 0;
+    if (c.fam == FAM_BF16) {
+      if (grouped)
+        n = f32out ? pair_max_clusters<IN_BF16, float, 256, MAXP_GROUPED>(c.stages)
+                   : pair_max_clusters<IN_BF16, __nv_bfloat16, 256, MAXP_GROUPED>(c.stages);
+      else
+        n = f32out ? pair_max_clusters<IN_BF16, float, 256, 1>(c.stages)
+                   : pair_max_clusters<IN_BF16, __nv_bfloat16, 256, 1>(c.stages);
+    } else {
+      n = f32out ? pair_max_clusters<IN_E4M3, float, 256, 1>(c.stages)
+                 : pair_max_clusters<IN_E4M3, __nv_bfloat16, 256, 1>(c.stages);
+    }
+    slot = n > 0 ? n : -1;
+  }
+  return slot;
+}
+
+// Shared driver of sk_gemm / sk_gemm_grouped / sk_gemm_backward.
+sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void *ws, size_t ws_bytes,
+              cudaStream_t st, int maxp) {
+  t_last_error.clear();
+  if (!problems || count < 1 || count > maxp) return SK_ERR_INVALID_ARG;
   int dev;
   DevInfo di;
   sk_status rc = current_device(&dev, &di);
@@ -495,27 +595,19 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
     cudaError_t e = cudaSetDevice(dev);
     if (e != cudaSuccess) return fail_cuda("cudaSetDevice", e);
   }
-  Cfg c;
-  rc = resolve_cfg(fam, cfg, di.sms, &c);
-  if (rc != SK_OK) return rc;
-
   // Validate everything before launching anything.
+  Cfg c;
   std::vector<Norm> work, scale_only;
   std::vector<int> idx;
-  for (int i = 0; i < count; ++i) {
-    const sk_problem &p = problems[i];
-    if (p.m == 0 || p.n == 0) continue;
-    Norm n = normalise(p);
-    if (p.k == 0) {
-      scale_only.push_back(n);   // C = beta * C_in: nothing to accumulate
-      continue;
-    }
-    if (fam != FAM_F32) {
-      rc = check_tc_alignment(n);
-      if (rc != SK_OK) return rc;
-    }
-    work.push_back(n);
-    idx.push_back(i);
+  rc = prepare(problems, count, cfg, di.sms, maxp, &c, &work, &idx, &scale_only);
+  if (rc != SK_OK) return rc;
+  const bool grouped = !(work.size() == 1 && maxp == 1);
+  if (c.pair && !work.empty()) {
+    // All units must be co-resident (owners wait on peers): never more
+    // pairs than the GPU can hold at once.
+    const int maxc = pair_clusters(dev, c, work[0].c_type == SK_F32, grouped);
+    if (maxc <= 0) return fail_msg(SK_ERR_UNSUPPORTED, "the CTA-pair kernel cannot be made resident");
+    c.g = std::min(c.g, maxc);
   }
   if (!work.empty()) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return SK_ERR_INVALID_ARG;
@@ -529,40 +621,31 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   PlanOut pl;
   build_plan(work, idx, c, &pl);
   Workspace w = carve(ws, c);
-  if (fam == FAM_F32) {
-    return work.size() == 1 && maxp == 1 ? launch_f32_family<1>(work, pl, c, w, st)
-                                         : launch_f32_family<MAXP_GROUPED>(work, pl, c, w, st);
+  if (c.fam == FAM_F32) {
+    return grouped ? launch_f32_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_f32_family<1>(work, pl, c, w, st);
   }
-  return work.size() == 1 && maxp == 1 ? launch_tc_family<1>(work, pl, c, w, st)
-                                       : launch_tc_family<MAXP_GROUPED>(work, pl, c, w, st);
+  return grouped ? launch_tc_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_tc_family<1>(work, pl, c, w, st);
 }
 
-// Plan for queries: honours num_sms > 0 without touching a device.
+// Plan for queries: honours num_sms > 0 without touching a device (the
+// pair kernel is then assumed to fit num_sms / 2 pairs).
 sk_status plan_for_query(const sk_problem *problems, int count, const sk_config *cfg, int num_sms, Cfg *c,
                          PlanOut *pl) {
-  if (!problems || count < 1 || count > MAXP_GROUPED) return SK_ERR_INVALID_ARG;
-  for (int i = 0; i < count; ++i) {
-    sk_status rc = check_problem(&problems[i]);
-    if (rc != SK_OK) return rc;
-  }
-  const Family fam = family_of(problems[0]);
   int sms = num_sms;
+  int dev = -1;
   if (sms <= 0) {
-    int dev;
     DevInfo di;
     sk_status rc = current_device(&dev, &di);
     if (rc != SK_OK) return rc;
     sms = di.sms;
   }
-  sk_status rc = resolve_cfg(fam, cfg, sms, c);
-  if (rc != SK_OK) return rc;
   std::vector<Norm> work;
   std::vector<int> idx;
-  for (int i = 0; i < count; ++i) {
-    const sk_problem &p = problems[i];
-    if (p.m == 0 || p.n == 0 || p.k == 0) continue;
-    work.push_back(normalise(p));
-    idx.push_back(i);
+  sk_status rc = prepare(problems, count, cfg, sms, MAXP_GROUPED, c, &work, &idx, nullptr);
+  if (rc != SK_OK) return rc;
+  if (c->pair && dev >= 0 && !work.empty()) {
+    const int maxc = pair_clusters(dev, *c, work[0].c_type == SK_F32, count > 1);
+    if (maxc > 0) c->g = std::min(c->g, maxc);
   }
   build_plan(work, idx, *c, pl);
   return SK_OK;

@@ -121,20 +121,22 @@ def _lib_schedule(sk, problems_shapes, cfg, sms, dtype="bf16"):
 _ROLE = {0: "whole", 1: "owner", 2: "peer", 3: "dp"}
 
 
-def _compare(sk, shapes, mode, sms, dtype="bf16", tile_n=0, min_ipu=1):
-    cfg = {"mode": mode, "tile_n": tile_n, "min_iters_per_unit": min_ipu}
+def _compare(sk, shapes, mode, sms, dtype="bf16", tile_n=0, min_ipu=1, tile_m=0):
+    cfg = {"mode": mode, "tile_n": tile_n, "min_iters_per_unit": min_ipu, "tile_m": tile_m}
     info, units = _lib_schedule(sk, shapes, cfg, sms, dtype)
     BM, BN, BK = info.tile_m, info.tile_n, info.tile_k
     problems = []
     for (M, N, K) in shapes:
         tm, tn = sch.tile_grid(M, N, BM, BN)
         problems.append((tm * tn, -(-K // BK)))
-    plan = sch.simulate(problems, sms, mode, min_iters_per_unit=min_ipu)
+    g = info.num_ctas              # units: CTAs, or CTA pairs for 256-row tiles
+    assert g == (sms // 2 if BM == 256 else sms)
+    plan = sch.simulate(problems, g, mode, min_iters_per_unit=min_ipu)
     assert info.sk_tiles == plan.sk_tiles
     assert info.sk_iters == plan.sk_iters
     assert info.sk_units == plan.sk_units
     assert info.tiles == len(plan.tiles)
-    for u in range(sms):
+    for u in range(g):
         exp = [(s.tile, s.problem, s.local_tile, s.k0, s.k1, s.role,
                 (s.peers[0], s.peers[-1]) if s.role == "owner" else None)
                for s in plan.units[u]]
@@ -172,6 +174,27 @@ def test_host_scheduler_matches_simulator_random(sk, mode):
         sms = rnd.randint(1, 152)
         _compare(sk, shapes, mode, sms, dtype=rnd.choice(["bf16", "f32", "e4m3"]),
                  min_ipu=rnd.choice([1, 1, 4]))
+
+
+def test_tile_selection(sk):
+    B = sk.binding
+    # K-major operands and m >= 256: CTA pairs with 256 x 256 tiles
+    info = _q(sk, sk.shape_problem(3840, 4096, 4096))[1]
+    assert (info.tile_m, info.tile_n, info.num_ctas) == (256, 256, 74)
+    # m < 256, transposed operands, or FP32: 128-row tiles on every CTA
+    for p in (sk.shape_problem(128, 8192, 16384), sk.shape_problem(4096, 4096, 4096, a_layout="col"),
+              sk.shape_problem(384, 384, 2048, dtype="f32")):
+        info = _q(sk, p)[1]
+        assert (info.tile_m, info.num_ctas) == (128, 148)
+    # asking for pairs with transposed operands is refused
+    assert _q(sk, sk.shape_problem(4096, 4096, 4096, b_layout="row"), {"tile_m": 256})[0] == B.SK_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("tile_m", [128, 256])
+def test_host_scheduler_explicit_tiles(sk, tile_m):
+    for mode in sch.MODES:
+        for shape in [(3840, 4096, 4096), (2048, 7168, 1024), (300, 700, 5000)]:
+            _compare(sk, [shape], mode, 152, tile_m=tile_m)
 
 
 def test_host_scheduler_unit_count_sweep(sk):

@@ -38,26 +38,38 @@ def test_bf16_first_small_dp(m):
     assert np.array_equal(to_np(c), ref)
 
 
-@pytest.mark.parametrize("tile_n", [128, 256])
+def test_bf16_pair_first_small_dp(m):
+    """Smallest CTA-pair case first: one whole 256x256 tile, DP, FP32 output."""
+    a, b = workloads.gemm_inputs(256, 256, 64, dtype="bf16", seed=0, dist="int")
+    c = _run(m, a, b, out_dtype=torch.float32, config=m.Config(mode="dp", tile_m=256))
+    ref, _ = oracle.gemm(a, b)
+    assert np.array_equal(to_np(c), ref)
+
+
+TILES = [(128, 128), (128, 256), (256, 256)]
+
+
+@pytest.mark.parametrize("tile", TILES)
 @pytest.mark.parametrize("mode", MODES)
-def test_bf16_small_int_exact(m, mode, tile_n):
+def test_bf16_small_int_exact(m, mode, tile):
     """Integer inputs in [-2, 2]: every product and partial sum is exact in
     FP32, so the FP32-output result must equal the oracle bit for bit."""
     a, b = workloads.gemm_inputs(384, 768, 2048, dtype="bf16", seed=1, dist="int")
     ref, _ = oracle.gemm(a, b)
-    c = _run(m, a, b, out_dtype=torch.float32, config=m.Config(mode=mode, tile_n=tile_n))
-    assert np.array_equal(to_np(c), ref), (mode, tile_n)
+    c = _run(m, a, b, out_dtype=torch.float32, config=m.Config(mode=mode, tile_m=tile[0], tile_n=tile[1]))
+    assert np.array_equal(to_np(c), ref), (mode, tile)
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", [(300, 520, 1000), (1920, 2000, 2000), (480, 512, 512), (129, 1000, 4160)])
-def test_bf16_bound_modes(m, mode, shape):
+def test_bf16_bound_modes(m, mode, shape, tile_m):
     M, N, K = shape
     a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=2)
-    c = _run(m, a, b, config=m.Config(mode=mode))
-    assert_within_bound(c, a, b, out="bf16", what=f"{shape} {mode}")
-    c32 = _run(m, a, b, out_dtype=torch.float32, config=m.Config(mode=mode))
-    assert_within_bound(c32, a, b, out="f32", what=f"{shape} {mode} f32-out")
+    c = _run(m, a, b, config=m.Config(mode=mode, tile_m=tile_m))
+    assert_within_bound(c, a, b, out="bf16", what=f"{shape} {mode} {tile_m}")
+    c32 = _run(m, a, b, out_dtype=torch.float32, config=m.Config(mode=mode, tile_m=tile_m))
+    assert_within_bound(c32, a, b, out="f32", what=f"{shape} {mode} {tile_m} f32-out")
 
 
 def test_bf16_identity(m):
@@ -81,14 +93,15 @@ def test_bf16_rank_one(m):
     assert np.array_equal(to_np(c), K * np.outer(u.numpy(), v.numpy()))
 
 
-def test_bf16_unit_count_sweep(m):
+@pytest.mark.parametrize("tile_m", [128, 256])
+def test_bf16_unit_count_sweep(m, tile_m):
     sms = torch.cuda.get_device_properties(dev()).multi_processor_count
     a, b = workloads.gemm_inputs(384, 768, 4096, dtype="bf16", seed=6, dist="int")
     ref, _ = oracle.gemm(a, b)
-    for g in sorted({1, 2, 3, 7, sms // 2, sms - 1, sms}):
+    for g in sorted({2, 3, 4, 7, 14, sms // 2, sms - 1, sms} | ({1} if tile_m == 128 else set())):
         for mode in ("sk", "hybrid2"):
             c = _run(m, a, b, out_dtype=torch.float32,
-                     config=m.Config(mode=mode, num_ctas=g, min_iters_per_unit=1))
+                     config=m.Config(mode=mode, num_ctas=g, min_iters_per_unit=1, tile_m=tile_m))
             assert np.array_equal(to_np(c), ref), (g, mode)
 
 
@@ -144,10 +157,11 @@ def test_bf16_deterministic(m):
     a, b = workloads.gemm_inputs(1536, 1536, 8192, dtype="bf16", seed=11)
     d = dev()
     ad, bd = a.to(d), b.to(d)
-    for mode in ("sk", "hybrid2"):
-        c1 = m.gemm(ad, bd, config=m.Config(mode=mode))
-        c2 = m.gemm(ad, bd, config=m.Config(mode=mode))
-        assert torch.equal(c1, c2), mode
+    for tile_m in (128, 256):
+        for mode in ("sk", "hybrid2"):
+            c1 = m.gemm(ad, bd, config=m.Config(mode=mode, tile_m=tile_m))
+            c2 = m.gemm(ad, bd, config=m.Config(mode=mode, tile_m=tile_m))
+            assert torch.equal(c1, c2), (mode, tile_m)
 
 
 def test_bf16_timeout_status_and_recovery(m):
@@ -155,12 +169,14 @@ def test_bf16_timeout_status_and_recovery(m):
     a, b = workloads.gemm_inputs(512, 512, 4096, dtype="bf16", seed=12)
     ad, bd = a.to(d), b.to(d)
     ws = m.Workspace(d)
-    m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1), workspace=ws)
-    assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT
-    m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
-    c = m.gemm(ad, bd, config=m.Config(mode="sk"), workspace=ws)
-    assert ws.status() == 0
-    assert_within_bound(c, a, b, out="bf16", what="after timeout")
+    for tile_m in (128, 256):
+        m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1, tile_m=tile_m),
+               workspace=ws)
+        assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT
+        m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
+        c = m.gemm(ad, bd, config=m.Config(mode="sk", tile_m=tile_m), workspace=ws)
+        assert ws.status() == 0
+        assert_within_bound(c, a, b, out="bf16", what=f"after timeout {tile_m}")
 
 
 @pytest.mark.parametrize("shape", workloads.BF16_SWEEP)
@@ -177,3 +193,5 @@ def test_bf16_sweep_full_size_sampled(m, shape):
     assert_sampled(c, a, b, out="bf16", what=str(shape))
     cdp = m.gemm(a, b, config=m.Config(mode="dp"))
     assert_sampled(cdp, a, b, out="bf16", what=str(shape) + " dp")
+    c128 = m.gemm(a, b, config=m.Config(tile_m=128))
+    assert_sampled(c128, a, b, out="bf16", what=str(shape) + " 128-row tiles")

@@ -44,9 +44,10 @@ def _quant(m, x, d):
     return q, s
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("shape", [(256, 512, 1024), (300, 520, 1024), (1024, 1024, 4096)])
 @pytest.mark.parametrize("mode", ["sk", "hybrid2", "dp"])
-def test_fp8_gemm_vs_dequantised(m, shape, mode):
+def test_fp8_gemm_vs_dequantised(m, shape, mode, tile_m):
     M, N, K = shape
     d = dev()
     xa = workloads.normal((M, K), seed=70)
@@ -55,7 +56,7 @@ def test_fp8_gemm_vs_dequantised(m, shape, mode):
     qb, sb = _quant(m, xb, d)
     A = qa.view(torch.float8_e4m3fn)
     Bm = qb.view(torch.float8_e4m3fn).t()
-    c = m.gemm(A, Bm, out_dtype=torch.float32, scale_a=sa, scale_b=sb, config=m.Config(mode=mode))
+    c = m.gemm(A, Bm, out_dtype=torch.float32, scale_a=sa, scale_b=sb, config=m.Config(mode=mode, tile_m=tile_m))
     assert m.default_workspace(d).status() == 0
     deq_a = fp8.dequantize_e4m3(qa.cpu().numpy(), sa.item())
     deq_b = fp8.dequantize_e4m3(qb.cpu().numpy(), sb.item()).T

@@ -36,6 +36,24 @@ def test_grouped_int_exact(m, mode):
         assert np.array_equal(to_np(o), r), (mode, SHAPES[i])
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
+def test_grouped_pair_tiles_exact(m, tile_m):
+    """Grouped launch whose problems all allow the CTA-pair kernel."""
+    d = dev()
+    shapes = [(256, 1024, 1024), (300, 512, 2048), (1024, 768, 128), (512, 2048, 64), (777, 256, 4096)]
+    As, Bs, refs = [], [], []
+    for i, (M, N, K) in enumerate(shapes):
+        a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=80 + i, dist="int")
+        As.append(a.to(d))
+        Bs.append(b.to(d))
+        refs.append(oracle.gemm(a, b)[0])
+    for mode in ("sk", "hybrid2", "dp"):
+        outs = m.grouped_gemm(As, Bs, out_dtype=torch.float32, config=m.Config(mode=mode, tile_m=tile_m))
+        assert m.default_workspace(d).status() == 0
+        for i, (o, r) in enumerate(zip(outs, refs)):
+            assert np.array_equal(to_np(o), r), (mode, tile_m, shapes[i])
+
+
 def test_grouped_bound_and_graph(m):
     d = dev()
     shapes = workloads.grouped_shapes(count=12, seed=0, m_hi=1024)
