@@ -69,7 +69,8 @@ typedef enum { SK_ROW_MAJOR = 0, SK_COL_MAJOR = 1 } sk_layout;
  *  HYBRID1 : (tiles mod CTAs) tiles Stream-K, the rest in whole DP waves.
  *  HYBRID2 : (CTAs + tiles mod CTAs) tiles Stream-K ("two-tile" Stream-K),
  *            the rest in whole DP waves; all Stream-K when tiles <= CTAs.
- *  AUTO    : the library's choice (currently HYBRID2).                    */
+ *  AUTO    : the library's choice: the mode (and, if left 0, the tile) its
+ *            runtime model predicts fastest for the problem set.          */
 typedef enum {
     SK_MODE_AUTO = 0,
     SK_MODE_DP = 1,
@@ -110,9 +111,10 @@ typedef struct {
     int tile_m;              /* 128, or 256 = CTA-pair kernel (two CTAs of a cluster
                                 share one 256 x tile_n tile through tcgen05
                                 cta_group::2; BF16/E4M3 with A row-major and B
-                                column-major only); 0 = automatic (256 when every
-                                problem allows it and has m >= 256) */
-    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (default 256; pair: 256) */
+                                column-major only); 0 = chosen by the library's
+                                runtime model */
+    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (pair: 256); 0 = chosen
+                                by the library's runtime model */
     int stages;              /* smem pipeline depth (BF16/E4M3: 2..6; default by tile) */
     sk_mode mode;            /* decomposition; default AUTO */
     int num_ctas;            /* persistent CTAs, 1 <= num_ctas <= SM count; 0 = SM count.
@@ -138,6 +140,7 @@ typedef struct {
     int64_t iters_per_unit;  /* floor(sk_iters / sk_units) */
     int64_t extra_units;     /* sk_iters mod sk_units: units with one more */
     size_t workspace_bytes;
+    double predicted_us;     /* the library's runtime-model estimate of the call */
 } sk_plan_info;
 
 /* One unit of work of one CTA, in the order that CTA processes it. */

@@ -61,6 +61,7 @@ class sk_plan_info(ctypes.Structure):
         ("tiles", ctypes.c_int64), ("sk_tiles", ctypes.c_int64), ("dp_tiles", ctypes.c_int64),
         ("sk_iters", ctypes.c_int64), ("iters_per_unit", ctypes.c_int64),
         ("extra_units", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
+        ("predicted_us", ctypes.c_double),
     ]
 
 

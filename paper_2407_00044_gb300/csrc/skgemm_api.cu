@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -249,17 +250,6 @@ Workspace carve(void *ws, const Cfg &c) {
   return w;
 }
 
-// Default tile when the caller leaves tile_m = 0: the CTA-pair kernel
-// (256-row tiles, half the per-SM operand traffic) when every problem has
-// K-major operands and at least 256 rows; otherwise 128-row tiles.
-int auto_tile_m(Family fam, const std::vector<Norm> &work) {
-  if (fam == FAM_F32 || work.empty()) return 128;
-  for (const Norm &n : work) {
-    if (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR) return 128;
-    if (n.M < 256) return 128;
-  }
-  return 256;
-}
 
 // -------------------------------------------------------------------- plan
 struct PlanOut {
@@ -267,6 +257,7 @@ struct PlanOut {
   std::vector<ProbSched> ps;
   std::vector<int> orig_index;   // problem index in the caller's array
   int grid;
+  double predicted_ns = 0;
 };
 
 int64_t count_sk_tiles(int64_t T, int64_t g, sk_mode mode) {
@@ -330,6 +321,63 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
   const int64_t dp = tiles - s.sk_tiles;
   const int64_t units = std::max<int64_t>(s.sk_units, std::min<int64_t>(c.g, dp));
   out->grid = (int)(c.pair ? 2 * units : units);
+}
+
+// ----------------------------------------------------------- runtime model
+// Analytic makespan of a plan, used to choose the tile and the DP/SK split
+// when the caller leaves them to the library (the paper's Results and
+// Future Work name such a predictive load-balancing model, "Block2Time").
+// Each unit's time is the sum over its work items of
+//   k-blocks x t_iter + t_item + (owner: peers x t_peer) + (peer: t_spill),
+// the kernel's time is the slowest unit plus a launch cost, and never less
+// than the algorithmic DRAM bytes at HBM bandwidth.  The per-k-block times
+// are measured steady-state figures of these kernels on GB300 (8192^3:
+// 0.355 us per 256x256x64 pair step, 0.40 us per 128x256x64 CTA step).
+struct ModelCoeffs {
+  double iter_ns, item_ns, spill_ns, peer_ns, launch_ns;
+};
+
+ModelCoeffs model_coeffs(const Cfg &c) {
+  ModelCoeffs m;
+  if (c.fam == FAM_F32) {
+    m = {1700.0, 500.0, 300.0, 300.0, 4000.0};
+  } else if (c.pair) {
+    m = {355.0, 400.0, 900.0, 900.0, 5000.0};
+  } else if (c.BN == 256) {
+    m = {400.0, 300.0, 900.0, 900.0, 4000.0};
+  } else {
+    m = {215.0, 250.0, 450.0, 450.0, 4000.0};
+  }
+  return m;
+}
+
+double algorithmic_dram_bytes(const std::vector<Norm> &work) {
+  double b = 0;
+  for (const Norm &n : work) {
+    const double es = dtype_bytes(n.in_type), cs = dtype_bytes(n.c_type);
+    b += (double)(n.M * n.K + n.K * n.N) * es + (double)n.M * n.N * cs * (n.beta != 0.f ? 2.0 : 1.0);
+  }
+  return b;
+}
+
+constexpr double kHbmBytesPerNs = 6500.0;   // measured copy bandwidth ~6.76 TB/s, rounded down
+
+double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
+  const ModelCoeffs k = model_coeffs(c);
+  double crit = 0;
+  for (int u = 0; u < c.g; ++u) {
+    Cursor cur;
+    cursor_init(pl.s, u, cur);
+    Item w;
+    double t = 0;
+    while (pl.s.num_problems > 0 && cursor_next(pl.s, pl.ps.data(), u, cur, w)) {
+      t += (w.k1 - w.k0) * k.iter_ns + k.item_ns;
+      if (w.role == ROLE_OWNER) t += (w.peer_last - w.peer_first + 1) * k.peer_ns;
+      if (w.role == ROLE_PEER) t += k.spill_ns;
+    }
+    crit = std::max(crit, t);
+  }
+  return k.launch_ns + std::max(crit, algorithmic_dram_bytes(work) / kHbmBytesPerNs);
 }
 
 // --------------------------------------------------------------- launches
@@ -502,6 +550,92 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
   return cuda_err(e, "FP32 GEMM launch");
 }
 
+// Fills the fields the caller left to the library (tile_m = 0, tile_n = 0,
+// mode = AUTO) with the candidate the runtime model predicts fastest.
+// Decisions are cached per problem set and config.
+sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vector<int> &idx, int sms,
+                      sk_config *d) {
+  const bool free_tile_m = d->tile_m == 0;
+  const bool free_tile_n = d->tile_n == 0 && fam != FAM_F32;
+  const bool free_mode = d->mode == SK_MODE_AUTO;
+  if (!free_tile_m && !free_tile_n && !free_mode) return SK_OK;
+  if (work.empty()) {
+    if (free_tile_m) d->tile_m = 128;
+    if (free_mode) d->mode = SK_MODE_HYBRID2;
+    return SK_OK;
+  }
+  // cache key
+  std::string key;
+  {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n, d->stages,
+                  (int)d->mode, d->num_ctas, d->min_iters_per_unit);
+    key = buf;
+    for (const Norm &n : work) {
+      std::snprintf(buf, sizeof(buf), "%lld,%lld,%lld,%d,%d,%d,%d;", (long long)n.M, (long long)n.N,
+                    (long long)n.K, (int)n.a_layout, (int)n.b_layout, (int)n.c_type, n.beta != 0.f);
+      key += buf;
+    }
+  }
+  static std::mutex mu;
+  static std::map<std::string, sk_config> cache;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      *d = it->second;
+      return SK_OK;
+    }
+  }
+  bool pair_ok = fam != FAM_F32 && (d->num_ctas > 0 ? d->num_ctas : sms) >= 2;
+  for (const Norm &n : work)
+    if (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR) pair_ok = false;
+  std::vector<int> tms, tns;
+  std::vector<sk_mode> modes;
+  if (free_tile_m) {
+    tms.push_back(128);
+    if (pair_ok && (d->tile_n == 0 || d->tile_n == 256)) tms.push_back(256);
+  } else {
+    tms.push_back(d->tile_m);
+  }
+  if (free_mode) modes = {SK_MODE_HYBRID2, SK_MODE_DP, SK_MODE_SK, SK_MODE_HYBRID1};
+  else modes = {d->mode};
+  double best = 1e300;
+  sk_config best_cfg = *d;
+  bool found = false;
+  for (int tm : tms) {
+    tns.clear();
+    if (fam == FAM_F32) tns.push_back(d->tile_n);
+    else if (!free_tile_n) tns.push_back(d->tile_n);
+    else if (tm == 256) tns.push_back(256);
+    else tns = {256, 128};
+    for (int tn : tns) {
+      for (sk_mode md : modes) {
+        sk_config t = *d;
+        t.tile_m = tm;
+        t.tile_n = tn;
+        t.mode = md;
+        Cfg c;
+        if (resolve_cfg(fam, &t, sms, &c) != SK_OK) continue;
+        PlanOut pl;
+        build_plan(work, idx, c, &pl);
+        const double ns = predict_ns(work, pl, c);
+        if (ns < best * 0.999) {   // keep the earlier candidate on near-ties
+          best = ns;
+          best_cfg = t;
+          found = true;
+        }
+      }
+    }
+  }
+  if (!found) return SK_ERR_UNSUPPORTED;
+  *d = best_cfg;
+  std::lock_guard<std::mutex> lk(mu);
+  if (cache.size() > 4096) cache.clear();
+  cache[key] = best_cfg;
+  return SK_OK;
+}
+
 // Normalises the problems, picks the tile (tile_m = 0: auto) and resolves
 // the config.  `work` gets the problems with m, n, k >= 1; `scale_only` the
 // ones with k == 0 (C = beta * C_in).
@@ -530,13 +664,9 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
   sk_config d;
   std::memset(&d, 0, sizeof(d));
   if (cfg) d = *cfg;
-  if (d.tile_m == 0) {
-    d.tile_m = auto_tile_m(fam, *work);
-    const int ctas = d.num_ctas > 0 ? d.num_ctas : sms;
-    if (ctas < 2) d.tile_m = 128;          // a pair needs two CTAs
-    if (d.tile_n == 128) d.tile_m = 128;   // pairs only come with 256-wide tiles
-  }
-  sk_status rc = resolve_cfg(fam, &d, sms, c);
+  sk_status rc = choose_auto(fam, *work, *idx, sms, &d);
+  if (rc != SK_OK) return rc;
+  rc = resolve_cfg(fam, &d, sms, c);
   if (rc != SK_OK) return rc;
   for (const Norm &n : *work) {
     if (fam != FAM_F32) {
@@ -648,6 +778,7 @@ sk_status plan_for_query(const sk_problem *problems, int count, const sk_config 
     if (maxc > 0) c->g = std::min(c->g, maxc);
   }
   build_plan(work, idx, *c, pl);
+  pl->predicted_ns = work.empty() ? 0.0 : predict_ns(work, *pl, *c);
   return SK_OK;
 }
 
@@ -794,6 +925,7 @@ sk_status sk_plan_query(const sk_problem *problems, int count, const sk_config *
   out->iters_per_unit = pl.s.q;
   out->extra_units = pl.s.r;
   out->workspace_bytes = ws_bytes_for(c);
+  out->predicted_us = pl.predicted_ns * 1e-3;
   return SK_OK;
 }
 
