@@ -603,6 +603,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   double best = 1e300;
   sk_config best_cfg = *d;
   bool found = false;
+  sk_status last_rc = SK_ERR_UNSUPPORTED;
   for (int tm : tms) {
     tns.clear();
     if (fam == FAM_F32) tns.push_back(d->tile_n);
@@ -616,7 +617,11 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
         t.tile_n = tn;
         t.mode = md;
         Cfg c;
-        if (resolve_cfg(fam, &t, sms, &c) != SK_OK) continue;
+        const sk_status rc = resolve_cfg(fam, &t, sms, &c);
+        if (rc != SK_OK) {
+          last_rc = rc;   // an invalid request stays invalid for every candidate
+          continue;
+        }
         PlanOut pl;
         build_plan(work, idx, c, &pl);
         const double ns = predict_ns(work, pl, c);
@@ -628,7 +633,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
       }
     }
   }
-  if (!found) return SK_ERR_UNSUPPORTED;
+  if (!found) return last_rc;
   *d = best_cfg;
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() > 4096) cache.clear();
