@@ -92,8 +92,19 @@ def test_workspace_size(sk):
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
     assert n.value == 256 + 768 + 148 * 128 * 128 * 4
     p = sk.shape_problem(384, 384, 2048)
+    c = sk.api._cfg({"num_ctas": 148, "tile_m": 128, "tile_n": 256})
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
     assert n.value == 256 + 768 + 148 * 128 * 256 * 4
+    # pairs: one 128 x 256 slot per CTA as well
+    c = sk.api._cfg({"num_ctas": 148, "tile_m": 256})
+    assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+    assert n.value == 256 + 768 + 148 * 128 * 256 * 4
+    # whatever the library picks fits the default workspace (every SM, 128 x 256 slots)
+    for shape in [(384, 384, 2048), (8192, 8192, 8192), (128, 8192, 16384)]:
+        c = sk.api._cfg({"num_ctas": 148})
+        q = sk.shape_problem(*shape)
+        assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+        assert n.value <= 256 + 768 + 148 * 128 * 256 * 4
 
 
 def test_gemm_without_device_reports_no_device(sk):
