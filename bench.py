@@ -387,10 +387,11 @@ def cpu_baseline(seconds: float = 12.0):
 def run_reference(args, world, rank):
     if rank != 0:
         return None
-    per_step = max(1.0, args.ref_step_seconds)
+    # each step is a bounded oracle sample; the whole run stays within ~2.5 minutes
+    per_step = max(0.2, min(args.ref_step_seconds, 150.0 / max(1, args.steps + args.warmup)))
     # warm-up steps (untimed), then timed steps, each a bounded oracle sample
     for _ in range(args.warmup):
-        cpu_baseline(seconds=min(per_step, 1.0))
+        cpu_baseline(seconds=per_step)
     vals = []
     t0 = time.perf_counter()
     last = None

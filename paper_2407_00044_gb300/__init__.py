@@ -14,7 +14,8 @@ from .api import (Config, Workspace, default_workspace, gemm, gemm_backward,  # 
                   grouped_gemm, layout_of, make_problem, plan, quantize_e4m3,
                   shape_problem, unit_items)
 from .autograd import SkMatmul, sk_matmul  # noqa: E402
+from . import autotune  # noqa: E402
 
 __all__ = ["binding", "SkError", "Config", "Workspace", "default_workspace", "gemm",
            "gemm_backward", "grouped_gemm", "layout_of", "make_problem", "plan",
-           "quantize_e4m3", "shape_problem", "unit_items", "SkMatmul", "sk_matmul"]
+           "quantize_e4m3", "shape_problem", "unit_items", "SkMatmul", "sk_matmul", "autotune"]
