@@ -200,7 +200,7 @@ def run_ours(args, world, rank, local):
         # read it back: the dirty lines are written back here, outside the
         # timed events, and L2 is left holding clean, unrelated lines.
         flush.fill_(float(i))
-        torch.sum(flush, out=flush_sink)
+        torch.sum(flush, dim=0, out=flush_sink)
 
     def one_pass(cfg, evs=None):
         for i, (a, b, c) in enumerate(data):

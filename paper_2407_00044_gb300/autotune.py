@@ -92,7 +92,7 @@ def _time_config(A, Bm, out, cfg, ws, warmup, iters, flush):
     for _ in range(iters):
         if flush is not None:
             flush[0].fill_(1.0)
-            torch.sum(flush[0], out=flush[1])
+            torch.sum(flush[0], dim=0, out=flush[1])
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)

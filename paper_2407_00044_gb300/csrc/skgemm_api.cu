@@ -577,13 +577,21 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
       key += buf;
     }
   }
+  // The cache holds only the chosen fields; everything else (timeouts,
+  // test flags, ...) stays the caller's.
+  struct Choice {
+    int tile_m, tile_n;
+    sk_mode mode;
+  };
   static std::mutex mu;
-  static std::map<std::string, sk_config> cache;
+  static std::map<std::string, Choice> cache;
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
     if (it != cache.end()) {
-      *d = it->second;
+      d->tile_m = it->second.tile_m;
+      d->tile_n = it->second.tile_n;
+      d->mode = it->second.mode;
       return SK_OK;
     }
   }
@@ -634,10 +642,12 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
     }
   }
   if (!found) return last_rc;
-  *d = best_cfg;
+  d->tile_m = best_cfg.tile_m;
+  d->tile_n = best_cfg.tile_n;
+  d->mode = best_cfg.mode;
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() > 4096) cache.clear();
-  cache[key] = best_cfg;
+  cache[key] = Choice{best_cfg.tile_m, best_cfg.tile_n, best_cfg.mode};
   return SK_OK;
 }
 
