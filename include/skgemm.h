@@ -125,7 +125,30 @@ typedef struct {
     int debug_flags;         /* test-only fault injection, 0 in normal use:
                                 bit 0 = peers never raise their flags, so every
                                 owner's bounded wait expires (SK_ERR_TIMEOUT) */
+    uint64_t *trace;         /* optional DEVICE buffer of SK_TRACE_BYTES_PER_CTA
+                                bytes per launched CTA (single-problem BF16 calls;
+                                ignored elsewhere):
+                                each CTA records its timeline there, see
+                                SK_TRACE_* below; NULL = no tracing */
 } sk_config;
+
+/* Timeline trace layout: CTA c owns entries [c*SK_TRACE_ENTRIES,
+ * (c+1)*SK_TRACE_ENTRIES), each two uint64: (event << 32 | item index) and
+ * %globaltimer in ns.  Entries 0..47 are written by the MMA issuer, 48..111
+ * by the epilogue, 112..115 by the roles' lead threads; unused entries keep
+ * the caller's contents (zero the buffer first). */
+#define SK_TRACE_ENTRIES 128
+#define SK_TRACE_BYTES_PER_CTA (SK_TRACE_ENTRIES * 16)
+enum {
+    SK_EV_START = 1,       /* CTA initialised (barriers, TMEM) */
+    SK_EV_MMA_BEGIN = 2,   /* item: accumulator free, MMAs about to start */
+    SK_EV_MMA_END = 4,     /* item: last MMA issued and committed */
+    SK_EV_EPI_BEGIN = 5,   /* item: accumulator complete, epilogue starts */
+    SK_EV_EPI_FLAGS = 6,   /* item (owner): every peer flag seen */
+    SK_EV_EPI_END = 7,     /* item: epilogue done (stores issued / flag raised) */
+    SK_EV_END = 8          /* a role is done (item = 0 producer, 1 MMA issuer,
+                              2 epilogue); the CTA ends at the latest of them */
+};
 
 /* Resolved plan of a call, for inspection and tests. */
 typedef struct {

@@ -28,6 +28,7 @@ class Config:
     min_iters_per_unit: int = 0
     timeout_ns: int = 0
     debug_flags: int = 0
+    trace: int = 0          # device pointer of a timeline buffer (see trace_gemm)
 
     def to_c(self) -> B.sk_config:
         c = B.sk_config()
@@ -39,6 +40,7 @@ class Config:
         c.min_iters_per_unit = self.min_iters_per_unit
         c.timeout_ns = self.timeout_ns
         c.debug_flags = self.debug_flags
+        c.trace = self.trace or None
         return c
 
 
@@ -268,3 +270,32 @@ def shape_problem(M: int, N: int, K: int, dtype: str = "bf16", out: str | None =
     p.A = p.B = p.C = 16   # non-null placeholders; plan queries never dereference
     p.alpha, p.beta = 1.0, 0.0
     return p
+
+
+def trace_gemm(A: torch.Tensor, Bm: torch.Tensor, out: torch.Tensor | None = None, config=None, **kw):
+    """Run one GEMM with per-CTA timeline tracing.  Returns (C, events)
+    where events[cta] is a time-sorted list of (event name, item, t_ns)
+    with t_ns relative to the earliest CTA start."""
+    import dataclasses
+    cfg = config or Config()
+    sms = torch.cuda.get_device_properties(A.device).multi_processor_count
+    buf = torch.zeros(sms * B.SK_TRACE_ENTRIES * 2, dtype=torch.int64, device=A.device)
+    cfg = dataclasses.replace(cfg, trace=buf.data_ptr())
+    C = gemm(A, Bm, out, config=cfg, **kw)
+    torch.cuda.synchronize()
+    raw = buf.view(sms, B.SK_TRACE_ENTRIES, 2).cpu()
+    t0 = None
+    per = []
+    for c in range(sms):
+        evs = []
+        for e in range(B.SK_TRACE_ENTRIES):
+            code, t = int(raw[c, e, 0]), int(raw[c, e, 1])
+            if code == 0:
+                continue
+            evs.append((B.TRACE_EVENTS.get(code >> 32, "?"), code & 0xFFFFFFFF, t))
+        evs.sort(key=lambda x: x[2])
+        if evs:
+            t0 = evs[0][2] if t0 is None else min(t0, evs[0][2])
+        per.append(evs)
+    per = [[(n, i, t - t0) for (n, i, t) in evs] for evs in per]
+    return C, per

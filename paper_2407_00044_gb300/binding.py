@@ -49,8 +49,13 @@ class sk_config(ctypes.Structure):
         ("tile_m", ctypes.c_int), ("tile_n", ctypes.c_int), ("stages", ctypes.c_int),
         ("mode", ctypes.c_int), ("num_ctas", ctypes.c_int),
         ("min_iters_per_unit", ctypes.c_int), ("timeout_ns", ctypes.c_uint64),
-        ("debug_flags", ctypes.c_int),
+        ("debug_flags", ctypes.c_int), ("trace", ctypes.c_void_p),
     ]
+
+SK_TRACE_ENTRIES = 128
+SK_TRACE_BYTES_PER_CTA = SK_TRACE_ENTRIES * 16
+TRACE_EVENTS = {1: "start", 2: "mma_begin", 4: "mma_end", 5: "epi_begin",
+                6: "epi_flags", 7: "epi_end", 8: "end"}
 
 
 class sk_plan_info(ctypes.Structure):

@@ -74,7 +74,19 @@ struct TcParams {
   uint64_t timeout_ns;
   int32_t stages;
   int32_t debug_flags;
+  uint64_t *trace;      // optional per-CTA timeline (SK_TRACE_* in skgemm.h)
 };
+
+constexpr int TRACE_ENTRIES = 128;
+constexpr int TRACE_MMA_BASE = 0, TRACE_EPI_BASE = 48, TRACE_CTA_BASE = 112;
+
+__device__ __forceinline__ void trace_put(uint64_t *trace, int entry, uint32_t ev, uint32_t item, uint64_t t) {
+  if (trace && entry >= 0 && entry < TRACE_ENTRIES) {
+    uint64_t *e = trace + ((uint64_t)blockIdx.x * TRACE_ENTRIES + entry) * 2;
+    e[0] = ((uint64_t)ev << 32) | item;
+    e[1] = t;
+  }
+}
 
 // Bytes of dynamic shared memory of a tcgen05 launch.  Never less than
 // 120 KB, so two CTAs can never share an SM: each CTA holds up to all 512
@@ -82,9 +94,14 @@ struct TcParams {
 // tcgen05.alloc behind its owner on the same SM would stall until timeout.
 inline int tc_smem_bytes(int bn, int stages) {
   const int stage = 128 * 128 + bn * 128;
-  const int need = 1024 /*alignment slack*/ + stages * stage + 256 /*barriers, TMEM slot*/;
+  const int need = 1024 /*alignment slack*/ + stages * stage + 512 /*barriers, TMEM slot*/;
   return need < 120 * 1024 ? 120 * 1024 : need;
 }
+
+// Owner fixup staged in shared memory: 16 KB units (one 32-column chunk of
+// one peer's partial), at most FIX_SMEM_UNITS in flight.
+constexpr int FIX_UNIT_BYTES = 128 * 32 * 4;
+constexpr int FIX_SMEM_UNITS = 12;
 
 template <int MAXP>
 cudaError_t launch_simt_f32(const SimtParams<MAXP> &p, int grid, cudaStream_t st);

@@ -23,7 +23,6 @@ constexpr int PAD = 4;
 struct F32Smem {
   float As[2][F32_BK][F32_BM + PAD];
   float Bs[2][F32_BK][F32_BN + PAD];
-  uint32_t timed_out;
 };
 
 // Load the 128 x 16 slice of an operand into registers.  `rows` index the
@@ -110,7 +109,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
     load_slice(pr.B, pr.b_cs, pr.b_rs, pr.b_kmajor, pr.b_vec, pr.N, pr.K, n0, w.k0 * F32_BK, rb);
     store_slice(sm.As[0], pr.a_kmajor, ra);
     store_slice(sm.Bs[0], pr.b_kmajor, rb);
-    __syncthreads();
+    cta_sync();
 
     for (int kb = w.k0; kb < w.k1; ++kb) {
       const int buf = (kb - w.k0) & 1;
@@ -139,7 +138,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
         store_slice(sm.As[buf ^ 1], pr.a_kmajor, ra);
         store_slice(sm.Bs[buf ^ 1], pr.b_kmajor, rb);
       }
-      __syncthreads();
+      cta_sync();
     }
 
     // Partial slot layout: float4 index v*256 + t, v = row_group*2 + col_half,
@@ -156,26 +155,28 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
           __stcg(slot + (i * 2 + h) * F32_THREADS + t,
                  make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]));
       __threadfence();
-      __syncthreads();
+      cta_sync();
       if (t == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + u, 1u);
       continue;
     }
 
     if (w.role == ROLE_OWNER) {
       if (t == 0) {
-        sm.timed_out = 0;
+        // Relaxed polls of every peer flag overlap; one acquire fence then
+        // orders the partial reads after the peers' release stores.
         const uint64_t t0 = globaltimer();
-        for (int p = w.peer_first; p <= w.peer_last && !sm.timed_out; ++p) {
-          while (ld_acquire_gpu(P.ws.flags + p) == 0u) {
-            if (globaltimer() - t0 > P.timeout_ns) {
-              atomicExch(P.ws.status, STATUS_TIMEOUT);
-              sm.timed_out = 1;
-              break;
-            }
+        for (;;) {
+          bool all = true;
+          for (int p = w.peer_first; p <= w.peer_last; ++p) all &= ld_relaxed_gpu(P.ws.flags + p) != 0u;
+          if (all) break;
+          if (globaltimer() - t0 > P.timeout_ns) {
+            atomicExch(P.ws.status, STATUS_TIMEOUT);
+            break;
           }
         }
+        fence_acq_rel_gpu();
       }
-      __syncthreads();
+      cta_sync();
       // Fixed summation order: own partial, then peers in ascending CTA index.
       for (int p = w.peer_first; p <= w.peer_last; ++p) {
         const float4 *slot = slot_base + (int64_t)p * slot_f4;
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
             acc[i][h * 4 + 3] += v.w;
           }
       }
-      __syncthreads();
+      cta_sync();
       if (t == 0)
         for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[p] = 0u;
     }

@@ -126,7 +126,7 @@ struct OutStore<__nv_bfloat16> {
 //   on both CTAs' barriers (multicast).  Each CTA's epilogue handles its own
 //   128 rows; both CTAs' epilogues release the leader's `tmem_empty`.  Each
 //   CTA of a pair has its own partial slot and flag (index 2*unit + rank).
-template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool TRACE>
 __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ TcParams<MAXP> P) {
   using Tr = InTraits<IN>;
   constexpr int BM = PAIR ? 256 : 128;          // tile rows per unit
@@ -153,7 +153,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *tfull_bar = bars + 2 * stages;
   uint64_t *tempty_bar = tfull_bar + 2;
   uint64_t *done_bar = tempty_bar + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done_bar + 1);
+  uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fix_bar + FIX_SMEM_UNITS);
   volatile uint32_t *abort_flag = tmem_slot + 1;
   const uint32_t tiles_addr = smem_u32(smem);
 
@@ -176,6 +177,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       mbar_init(smem_u32(tempty_bar + a), PAIR ? 8 : 4);
     }
     mbar_init(smem_u32(done_bar), 1);
+    for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
     *abort_flag = 0;
     fence_barrier_init();
     fence_proxy_async_smem();
@@ -190,10 +192,13 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     }
   }
   tc_fence_before();
-  __syncthreads();
+  cta_sync();
   if constexpr (PAIR) cluster_sync();   // the peer's barriers exist before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // Timeline tracing is compiled only into the TRACE instantiations.
+  uint64_t *const trace = TRACE ? P.trace : nullptr;
+  if (TRACE && threadIdx.x == 0) trace_put(trace, TRACE_CTA_BASE, 1, 0, globaltimer_ordered());
 
   auto fail = [&]() {
     *abort_flag = 1;
@@ -293,9 +298,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       cursor_init(S, u, c);
       Item w;
       bool ok = true;
+      int nitem = 0;
       while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
         const TcProblem &pr = P.prob[w.problem];
         const uint32_t idesc = IDESC | ((uint32_t)pr.a_mn << 15) | ((uint32_t)pr.b_mn << 16);
+        const int tr = TRACE_MMA_BASE + 3 * nitem;
         const bool got = PAIR ? mbar_wait_cluster(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo)
                               : mbar_wait(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo);
         if (!got) {
@@ -303,6 +310,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           break;
         }
         tc_fence_after();
+        if (TRACE && nitem < 16) trace_put(trace, tr, 2, nitem, globaltimer());
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
         for (int kb = w.k0; kb < w.k1; ++kb) {
           if (!mbar_wait(smem_u32(full_bar + stage), phase, tmo)) {
@@ -347,6 +355,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           mma_commit_pair_mc(smem_u32(tfull_bar + acc), (uint16_t)3);
         else
           mma_commit(smem_u32(tfull_bar + acc));
+        if (TRACE && nitem < 16) trace_put(trace, tr + 2, 4, nitem, globaltimer());
+        ++nitem;
         if (++acc == 2) {
           acc = 0;
           acc_phase ^= 1u;
@@ -383,13 +393,19 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           mbar_arrive(smem_u32(tempty_bar + a));
       }
     };
-    while (!*abort_flag && cursor_next(S, P.ps, u, c, w)) {
+    int nitem = 0;
+    const bool tr_lead = TRACE && et == 0;
+    // Loop exit and wait results are made warp-uniform: the lanes of an
+    // epilogue warp must stay converged for the warp-collective tcgen05.ld.
+    while (!__any_sync(0xffffffffu, *abort_flag != 0u) && cursor_next(S, P.ps, u, c, w)) {
       const TcProblem &pr = P.prob[w.problem];
-      if (!mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo)) {
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo))) {
         fail();
         break;
       }
       tc_fence_after();
+      const int tr = TRACE_EPI_BASE + 3 * nitem;
+      if (tr_lead && nitem < 21) trace_put(trace, tr, 5, nitem, globaltimer_ordered());
       const uint32_t tbase = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN);
 
       if (w.role == ROLE_PEER) {
@@ -406,23 +422,28 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         __threadfence();
         named_bar_sync(1, 128);
         if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + slot_id, 1u);
+        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       } else {
         // Peer units p hold their partial of this CTA's rows in slot
         // (PAIR ? 2p + rank : p).
         if (w.role == ROLE_OWNER) {
           if (et == 0) {
+            // Poll every peer's flag with relaxed loads (they overlap), then
+            // one acquire fence orders the partial reads after the peers'
+            // release stores.
             const uint64_t t0 = globaltimer();
-            bool to = false;
-            for (int p = w.peer_first; p <= w.peer_last && !to; ++p) {
-              const int ps = PAIR ? 2 * p + (int)rank : p;
-              while (ld_acquire_gpu(P.ws.flags + ps) == 0u) {
-                if (globaltimer() - t0 > tmo) {
-                  atomicExch(P.ws.status, STATUS_TIMEOUT);
-                  to = true;
-                  break;
-                }
+            for (;;) {
+              bool all = true;
+              for (int p = w.peer_first; p <= w.peer_last; ++p)
+                all &= ld_relaxed_gpu(P.ws.flags + (PAIR ? 2 * p + (int)rank : p)) != 0u;
+              if (all) break;
+              if (globaltimer() - t0 > tmo) {
+                atomicExch(P.ws.status, STATUS_TIMEOUT);
+                break;
               }
             }
+            fence_acq_rel_gpu();
+            if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           }
           named_bar_sync(1, 128);
         }
@@ -432,33 +453,98 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           if (pr.scale_b) alpha *= *pr.scale_b;
         }
         const int grow = w.tm * BM + (int)rank * 128 + row;
+        auto store_chunk = [&](int ch, const float (&v)[32]) {
+          if (grow < pr.M) {
+            const int gcol = w.tn * BN + ch * 32;
+            if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
+          }
+        };
+        if (w.role != ROLE_OWNER) {
 #pragma unroll 1
-        for (int ch = 0; ch < BN / 32; ++ch) {
+          for (int ch = 0; ch < BN / 32; ++ch) {
+            float v[32];
+            tmem_ld32(tbase + ch * 32, v);
+            store_chunk(ch, v);
+          }
+        } else if (c.it >= c.end && c.dp >= S.total_tiles) {
+          // This owner item is the CTA's last: every MMA has completed, so
+          // the operand ring in shared memory is free.  Stage the peers'
+          // partials there with bulk copies, 16 KB units (chunk, peer) in
+          // chunk-major order, up to FIX_SMEM_UNITS in flight; then add
+          // them in the fixed order (own accumulator, peers ascending).
+          constexpr int NCH = BN / 32;
+          const int np = w.peer_last - w.peer_first + 1;
+          const int nunits = NCH * np;
+          int nb = (stages * STAGE_BYTES) / FIX_UNIT_BYTES;
+          if (nb > FIX_SMEM_UNITS) nb = FIX_SMEM_UNITS;
           float v[32];
-          tmem_ld32(tbase + ch * 32, v);
-          if (w.role == ROLE_OWNER) {
-            // Fixed order: own accumulator, then peers in ascending unit index.
-            for (int p = w.peer_first; p <= w.peer_last; ++p) {
-              const float4 *slot = slots + (int64_t)(PAIR ? 2 * p + (int)rank : p) * SLOT_F4;
+          bool ok = true;
+          int group = 0;
+          for (int g0 = 0; g0 < nunits && ok; g0 += nb, ++group) {
+            const int gn = nunits - g0 < nb ? nunits - g0 : nb;
+            if (et == 0) {
+              fence_proxy_async_all();   // the acquired partials, to the copy engine
+              for (int b = 0; b < gn; ++b) {
+                const int i = g0 + b;
+                const int ch = i / np;
+                const int p = w.peer_first + (i - ch * np);
+                const float4 *src = slots + (int64_t)(PAIR ? 2 * p + (int)rank : p) * SLOT_F4 + (ch * 8) * 128;
+                const uint32_t fb = smem_u32(fix_bar + b);
+                mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
+                bulk_copy_g2s(tiles_addr + b * FIX_UNIT_BYTES, src, FIX_UNIT_BYTES, fb);
+              }
+            }
+            for (int b = 0; b < gn; ++b) {
+              const int i = g0 + b;
+              const int ch = i / np;
+              const int pi = i - ch * np;
+              if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(fix_bar + b), (uint32_t)(group & 1), tmo))) {
+                fail();
+                ok = false;
+                break;
+              }
+              if (pi == 0) tmem_ld32(tbase + ch * 32, v);
+              const float4 *sb = reinterpret_cast<const float4 *>(smem + b * FIX_UNIT_BYTES);
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                float4 q = __ldcg(slot + (ch * 8 + j) * 128 + row);
+                const float4 q = sb[j * 128 + row];
+                v[4 * j] += q.x;
+                v[4 * j + 1] += q.y;
+                v[4 * j + 2] += q.z;
+                v[4 * j + 3] += q.w;
+              }
+              if (pi == np - 1) store_chunk(ch, v);
+            }
+            named_bar_sync(1, 128);   // every thread is done with the group's buffers
+          }
+        } else {
+          // An owner item followed by more work: its fixup overlaps the next
+          // item's MMAs, so a plain loop suffices.  Fixed summation order:
+          // own accumulator, then peers in ascending unit index.
+#pragma unroll 1
+          for (int ch = 0; ch < BN / 32; ++ch) {
+            float v[32];
+            tmem_ld32(tbase + ch * 32, v);
+            for (int p = w.peer_first; p <= w.peer_last; ++p) {
+              const float4 *src = slots + (int64_t)(PAIR ? 2 * p + (int)rank : p) * SLOT_F4 + (ch * 8) * 128 + row;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 q = __ldcg(src + j * 128);
                 v[4 * j] += q.x;
                 v[4 * j + 1] += q.y;
                 v[4 * j + 2] += q.z;
                 v[4 * j + 3] += q.w;
               }
             }
-          }
-          if (grow < pr.M) {
-            const int gcol = w.tn * BN + ch * 32;
-            if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
+            store_chunk(ch, v);
           }
         }
         release_acc(acc);
         if (w.role == ROLE_OWNER && et == 0)
           for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[PAIR ? 2 * p + (int)rank : p] = 0u;
+        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       }
+      ++nitem;
       if (++acc == 2) {
         acc = 0;
         acc_phase ^= 1u;
@@ -467,7 +553,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   }
 
   tc_fence_before();
-  __syncthreads();
+  // Trace: each role's lead thread (producer 0, MMA issuer 1, epilogue 2)
+  // stamps when its role is done; the CTA ends at the latest of these.
+  // (A stamp taken right after a barrier can be read before the barrier
+  // completes, so none is taken there.)
+  if (TRACE) {
+    const int role_lead = threadIdx.x == 0 ? 0 : threadIdx.x == 32 ? 1 : threadIdx.x == 64 ? 2 : -1;
+    if (role_lead >= 0) trace_put(trace, TRACE_CTA_BASE + 1 + role_lead, 8, role_lead, globaltimer_ordered());
+  }
+  cta_sync();
   // A pair's leader MMAs read the peer's shared memory and write its TMEM:
   // neither CTA frees TMEM or exits before both are done.
   if constexpr (PAIR) cluster_sync();
@@ -480,9 +574,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   }
 }
 
-template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
-cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR>;
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool TRACE>
+cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, TRACE>;
   const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages);
   (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -509,10 +603,20 @@ cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
   }
 }
 
+// Tracing variants exist for single-problem BF16 launches; elsewhere a
+// trace buffer is ignored.
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
+cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
+  if constexpr (IN == IN_BF16 && MAXP == 1) {
+    if (p.trace) return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true>(p, grid, st);
+  }
+  return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, false>(p, grid, st);
+}
+
 // Co-resident clusters of two for the pair kernel (0 if it cannot launch).
 template <int IN, typename OutT, int BN, int MAXP>
 int pair_max_clusters(int stages) {
-  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, true>;
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, true, false>;
   const int smem = tc_smem_bytes(BN / 2, stages);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};

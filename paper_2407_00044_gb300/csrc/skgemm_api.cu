@@ -190,6 +190,7 @@ struct Cfg {
   int min_ipu;
   uint64_t timeout_ns;
   int debug_flags;
+  uint64_t *trace;
   int ctas() const { return pair ? 2 * g : g; }
 };
 
@@ -215,7 +216,7 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
     if (r.pair && r.BN != 256) return SK_ERR_UNSUPPORTED;
     r.BK = fam == FAM_BF16 ? 64 : 128;
     const int stage_bytes = 128 * 128 + (r.pair ? r.BN / 2 : r.BN) * 128;   // per CTA
-    const int max_stages = std::min(6, (227 * 1024 - 1024 - 256) / stage_bytes);
+    const int max_stages = std::min(6, (227 * 1024 - 1024 - 512) / stage_bytes);
     r.stages = d.stages ? d.stages : max_stages;
     if (r.stages < 2 || r.stages > max_stages) return SK_ERR_UNSUPPORTED;
   }
@@ -230,6 +231,7 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.min_ipu = d.min_iters_per_unit ? d.min_iters_per_unit : 4;
   r.timeout_ns = d.timeout_ns ? d.timeout_ns : 2000000000ull;
   r.debug_flags = d.debug_flags;
+  r.trace = d.trace;
   *out = r;
   return SK_OK;
 }
@@ -331,22 +333,29 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 //   k-blocks x t_iter + t_item + (owner: peers x t_peer) + (peer: t_spill),
 // the kernel's time is the slowest unit plus a launch cost, and never less
 // than the algorithmic DRAM bytes at HBM bandwidth.  The per-k-block times
-// are measured steady-state figures of these kernels on GB300 (8192^3:
-// 0.355 us per 256x256x64 pair step, 0.40 us per 128x256x64 CTA step).
+// are measured figures of these kernels on GB300 (8192^3: 0.345 us per
+// 256x256x64 pair step with 6 stages, 0.40 us per 128x256x64 CTA step; a
+// 128x128x64 step also costs ~0.40 us: it is bound by shared-memory
+// bandwidth, not the tensor pipe).
 struct ModelCoeffs {
-  double iter_ns, item_ns, spill_ns, peer_ns, launch_ns;
+  double iter_ns;     // one k-block of one tile
+  double item_ns;     // per work item (tile switch, epilogue not hidden)
+  double spill_ns;    // peer: write the FP32 partial and release the flag
+  double owner_ns;    // owner: flag wait and the first batch of partial reads
+  double peer_ns;     // owner: each further peer partial
+  double launch_ns;   // launch, prologue, pipeline fill and the last epilogue
 };
 
 ModelCoeffs model_coeffs(const Cfg &c) {
   ModelCoeffs m;
   if (c.fam == FAM_F32) {
-    m = {1700.0, 500.0, 300.0, 300.0, 4000.0};
+    m = {1700.0, 500.0, 300.0, 1500.0, 300.0, 6000.0};
   } else if (c.pair) {
-    m = {355.0, 400.0, 900.0, 900.0, 5000.0};
+    m = {c.stages >= 6 ? 345.0 : 370.0, 400.0, 1000.0, 3000.0, 400.0, 10000.0};
   } else if (c.BN == 256) {
-    m = {400.0, 300.0, 900.0, 900.0, 4000.0};
+    m = {400.0, 300.0, 1000.0, 3000.0, 400.0, 9000.0};
   } else {
-    m = {215.0, 250.0, 450.0, 450.0, 4000.0};
+    m = {400.0, 250.0, 500.0, 2000.0, 250.0, 9000.0};
   }
   return m;
 }
@@ -372,7 +381,7 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
     double t = 0;
     while (pl.s.num_problems > 0 && cursor_next(pl.s, pl.ps.data(), u, cur, w)) {
       t += (w.k1 - w.k0) * k.iter_ns + k.item_ns;
-      if (w.role == ROLE_OWNER) t += (w.peer_last - w.peer_first + 1) * k.peer_ns;
+      if (w.role == ROLE_OWNER) t += k.owner_ns + (w.peer_last - w.peer_first) * k.peer_ns;
       if (w.role == ROLE_PEER) t += k.spill_ns;
     }
     crit = std::max(crit, t);
@@ -470,6 +479,7 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   P->timeout_ns = c.timeout_ns;
   P->stages = c.stages;
   P->debug_flags = c.debug_flags;
+  P->trace = c.trace;
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
   if (c.fam == FAM_BF16) {

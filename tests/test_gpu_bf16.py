@@ -195,3 +195,27 @@ def test_bf16_sweep_full_size_sampled(m, shape):
     assert_sampled(cdp, a, b, out="bf16", what=str(shape) + " dp")
     c128 = m.gemm(a, b, config=m.Config(tile_m=128))
     assert_sampled(c128, a, b, out="bf16", what=str(shape) + " 128-row tiles")
+
+
+def test_trace_timeline(m):
+    """Per-CTA timeline tracing: every launched CTA records start/end, every
+    item's MMA and epilogue events in order, and the result is unchanged."""
+    a, b = workloads.gemm_inputs(768, 1024, 2048, dtype="bf16", seed=13, dist="int")
+    d = dev()
+    ref, _ = oracle.gemm(a, b)
+    for tile_m in (128, 256):
+        c, ev = m.trace_gemm(a.to(d), b.to(d), out_dtype=torch.float32,
+                             config=m.Config(mode="sk", tile_m=tile_m))
+        assert np.array_equal(to_np(c), ref)
+        active = [e for e in ev if e]
+        assert len(active) >= 2
+        for evs in active:
+            names = [n for n, _, _ in evs]
+            assert names[0] == "start"
+            assert sorted(i for n, i, _ in evs if n == "end") == [0, 1, 2]   # every role reported
+            t_end = max(t for n, _, t in evs if n == "end")
+            assert all(t <= t_end for _, _, t in evs)
+            for it in {i for n, i, _ in evs if n == "mma_begin"}:
+                t = {n: tt for n, i, tt in evs if i == it and n != "start" and n != "end"}
+                if "epi_end" in t and "mma_begin" in t:
+                    assert t["mma_begin"] <= t["mma_end"] <= t["epi_end"]
