@@ -252,11 +252,13 @@ def run_ours(args, world, rank, local):
     value = total_flops / max_s / 1e12
 
     per_shape = []
-    for (M, N, K), f, t_sk, t_dp in zip(shapes, flops, sk_ms, dp_ms):
+    for (M, N, K), f, t_sk, t_dp, (a, b, c) in zip(shapes, flops, sk_ms, dp_ms, data):
         ms_sk = statistics.median(t_sk)
         ms_dp = statistics.median(t_dp)
+        info = sk.plan(sk.make_problem(a, b, c), auto)
         per_shape.append({
             "M": M, "N": N, "K": K,
+            "tile": f"{info.tile_m}x{info.tile_n}", "mode": ["auto", "dp", "sk", "hybrid1", "hybrid2"][info.mode],
             "ms": round(ms_sk, 4), "tflops": round(f / ms_sk / 1e9, 1),
             "pct_peak": round(100 * f / ms_sk / 1e9 / pk["bf16"], 1),
             "dp_ms": round(ms_dp, 4), "dp_tflops": round(f / ms_dp / 1e9, 1),
@@ -283,8 +285,8 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_ms, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic: seeded uniform[-1,1] rounded to BF16 (torch CUDA generator)",
-        "config": {"workload": WORKLOAD, "mode": "library default (two-tile Stream-K + DP hybrid)",
-                   "tile": "128x256x64, 4-stage TMA ring, 2 TMEM accumulators",
+        "config": {"workload": WORKLOAD,
+                   "mode": "library default: tile and DP/SK split chosen by the runtime model (per shape below)",
                    "l2": "flushed before every GEMM by writing then reading a 256 MB buffer (outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "dp_baseline": {"value": round(sum(flops) / (dp_step_ms / 1e3) / 1e12, 2), "unit": UNIT,
@@ -339,6 +341,148 @@ def run_e2e(sk, shapes, data, args, ws, world):
     tot, mx = aggregate(flops * steps, ms * steps / 1e3, world)
     return {"value": round(tot / mx / 1e12, 2), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(ms, 3)}
+
+
+# ------------------------------------------------- other workloads (info)
+def _timed_region(fn, steps, flush):
+    """Median ms of fn() over `steps` runs, L2 flushed before each."""
+    stream = torch.cuda.current_stream()
+    evs = []
+    for _ in range(steps):
+        flush()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return statistics.median(a.elapsed_time(b) for a, b in evs)
+
+
+def run_workload(args, world, rank, local):
+    """FP8, grouped and autograd configurations, measured like the sweep
+    (inputs resident, L2 flushed, CUDA events), each next to its
+    data-parallel counterpart."""
+    import paper_2407_00044_gb300 as sk
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pk = peaks()
+    flushbuf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+
+    def flush():
+        flushbuf.fill_(1.0)
+        torch.sum(flushbuf, dim=0, out=sink)
+
+    steps = max(3, min(args.steps, 50))
+    auto, dp = sk.Config(), sk.Config(mode="dp")
+    rows = []
+    if args.workload == "fp8":
+        peak = 2 * pk["bf16"]
+        peak_note = "2 x measured bf16 burst (no FP8 measurement available)"
+        for i, (M, N, K) in enumerate(workloads.FP8_SHAPES):
+            xa = workloads.device_normal((M, K), seed=2000 + 2 * i, device=dev)
+            xb = workloads.device_normal((N, K), seed=2001 + 2 * i, device=dev)
+            qa, sa = sk.quantize_e4m3(xa)
+            qb, sb = sk.quantize_e4m3(xb)
+            A, Bm = qa.view(torch.float8_e4m3fn), qb.view(torch.float8_e4m3fn).t()
+            C = torch.empty(M, N, dtype=torch.bfloat16, device=dev)
+            for cfg in (auto, dp):
+                for _ in range(args.warmup):
+                    sk.gemm(A, Bm, C, scale_a=sa, scale_b=sb, config=cfg)
+            t = _timed_region(lambda: sk.gemm(A, Bm, C, scale_a=sa, scale_b=sb, config=auto), steps, flush)
+            tdp = _timed_region(lambda: sk.gemm(A, Bm, C, scale_a=sa, scale_b=sb, config=dp), steps, flush)
+            rows.append((f"{M}x{N}x{K} e4m3", workloads.gemm_flops(M, N, K), t, tdp))
+        desc = "FP8 E4M3 per-tensor scaled, FP32 accumulate, BF16 out: " + " ".join(
+            f"({m},{n},{k})" for m, n, k in workloads.FP8_SHAPES)
+    elif args.workload == "grouped":
+        peak, peak_note = pk["bf16"], "measured bf16 burst"
+        shapes = workloads.grouped_shapes(count=64, seed=0)
+        As, Bs, Cs = [], [], []
+        for i, (M, N, K) in enumerate(shapes):
+            As.append(workloads.device_uniform((M, K), seed=3000 + 2 * i, device=dev))
+            Bs.append(workloads.device_uniform((N, K), seed=3001 + 2 * i, device=dev).t())
+            Cs.append(torch.empty(M, N, dtype=torch.bfloat16, device=dev))
+        graphs = {}
+        for name, cfg in (("auto", auto), ("dp", dp)):
+            sk.grouped_gemm(As, Bs, Cs, config=cfg)
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=s):
+                    sk.grouped_gemm(As, Bs, Cs, config=cfg)
+            torch.cuda.current_stream().wait_stream(s)
+            graphs[name] = g
+        # per-problem launches (one graph of 64 launches), the library's default each
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            for a, b, c in zip(As, Bs, Cs):
+                sk.gemm(a, b, c)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                for a, b, c in zip(As, Bs, Cs):
+                    sk.gemm(a, b, c)
+        torch.cuda.current_stream().wait_stream(s)
+        graphs["separate"] = g
+        for gg in graphs.values():
+            for _ in range(args.warmup):
+                gg.replay()
+        f = sum(workloads.gemm_flops(*x) for x in shapes)
+        t = _timed_region(graphs["auto"].replay, steps, flush)
+        tdp = _timed_region(graphs["dp"].replay, steps, flush)
+        tsep = _timed_region(graphs["separate"].replay, steps, flush)
+        rows.append(("grouped 64 (one launch)", f, t, tdp))
+        rows.append(("64 separate launches", f, tsep, tsep))
+        desc = ("grouped BF16: 64 problems, M log-uniform [64,4096], N,K from {1024,2048,4096,7168}, "
+                "one persistent launch replayed from a CUDA graph")
+    elif args.workload == "autograd":
+        peak, peak_note = pk["bf16"], "measured bf16 burst"
+        M, N, K = workloads.AUTOGRAD_SHAPE
+        A = workloads.device_uniform((M, K), seed=4000, device=dev).requires_grad_(True)
+        Bm = workloads.device_uniform((N, K), seed=4001, device=dev).t().detach().requires_grad_(True)
+        G = workloads.device_normal((M, N), seed=4002, device=dev, dtype=torch.bfloat16)
+
+        def step(cfg):
+            A.grad = None
+            Bm.grad = None
+            C = sk.sk_matmul(A, Bm, cfg)
+            C.backward(G)
+
+        for cfg in (auto, dp):
+            for _ in range(args.warmup):
+                step(cfg)
+        f = 3 * workloads.gemm_flops(M, N, K)
+        t = _timed_region(lambda: step(auto), steps, flush)
+        tdp = _timed_region(lambda: step(dp), steps, flush)
+        rows.append((f"{M}x{N}x{K} fwd+bwd", f, t, tdp))
+        desc = "autograd BF16 layer: forward C=A*B plus backward dA=dC*B^T, dB=A^T*dC"
+    else:
+        raise ValueError(args.workload)
+    if ws_status(sk, dev) != 0:
+        raise RuntimeError("device status")
+    tot_f = sum(r[1] for r in rows if not r[0].startswith("64 separate"))
+    tot_t = sum(r[2] for r in rows if not r[0].startswith("64 separate"))
+    tot_dp = sum(r[3] for r in rows if not r[0].startswith("64 separate"))
+    value = tot_f / (tot_t / 1e3) / 1e12
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": round(tot_t, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e4m3" if args.workload == "fp8" else "bf16", "data": "synthetic",
+        "config": {"workload": desc, "l2": "flushed (write then read 256 MB) before every timed run"},
+        "dp_baseline": {"value": round(tot_f / (tot_dp / 1e3) / 1e12, 2), "unit": UNIT},
+        "rows": [{"case": r[0], "ms": round(r[2], 4), "tflops": round(r[1] / r[2] / 1e9, 1),
+                  "pct_peak": round(100 * r[1] / r[2] / 1e9 / peak, 1), "dp_ms": round(r[3], 4),
+                  "dp_tflops": round(r[1] / r[3] / 1e9, 1)} for r in rows],
+        "peak": {"value": peak, "source": peak_note},
+    }
+
+
+def ws_status(sk, dev):
+    return sk.default_workspace(dev).status()
 
 
 # -------------------------------------------------------- CPU oracle arm
@@ -427,6 +571,8 @@ def main(argv=None):
     ap.add_argument("--mode", default="auto", choices=["auto", "dp", "sk", "hybrid1", "hybrid2"])
     ap.add_argument("--no-dp", dest="dp", action="store_false", help="skip the data-parallel baseline")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer run")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "fp8", "grouped", "autograd"],
+                    help="sweep (default, the headline) or one of the other configurations")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -436,7 +582,7 @@ def main(argv=None):
     else:
         if world > 1 or rank != 0:
             args.cpu_baseline = args.cpu_baseline and rank == 0 and world == 1
-        line = run_ours(args, world, rank, local)
+        line = run_ours(args, world, rank, local) if args.workload == "sweep" else run_workload(args, world, rank, local)
     if line is not None and rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -330,32 +330,37 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // when the caller leaves them to the library (the paper's Results and
 // Future Work name such a predictive load-balancing model, "Block2Time").
 // Each unit's time is the sum over its work items of
-//   k-blocks x t_iter + t_item + (owner: peers x t_peer) + (peer: t_spill),
+//   k-blocks x t_iter + t_item (+ fixup cost if the item is an owner, which
+//   lies on the critical path only when it is the CTA's last item, when
+//   every peer finishes at the same time and must spill first),
 // the kernel's time is the slowest unit plus a launch cost, and never less
-// than the algorithmic DRAM bytes at HBM bandwidth.  The per-k-block times
+// than the DRAM bytes its operand loads cost at HBM bandwidth (see
+// plan_dram_bytes: Stream-K ranges lose the L2 sharing of DP waves).  The per-k-block times
 // are measured figures of these kernels on GB300 (8192^3: 0.345 us per
 // 256x256x64 pair step with 6 stages, 0.40 us per 128x256x64 CTA step; a
 // 128x128x64 step also costs ~0.40 us: it is bound by shared-memory
 // bandwidth, not the tensor pipe).
 struct ModelCoeffs {
-  double iter_ns;     // one k-block of one tile
-  double item_ns;     // per work item (tile switch, epilogue not hidden)
-  double spill_ns;    // peer: write the FP32 partial and release the flag
-  double owner_ns;    // owner: flag wait and the first batch of partial reads
-  double peer_ns;     // owner: each further peer partial
-  double launch_ns;   // launch, prologue, pipeline fill and the last epilogue
+  double iter_ns;         // one k-block of one tile
+  double item_ns;         // per work item (tile switch, epilogue not hidden)
+  double launch_ns;       // launch, prologue, pipeline fill and the last epilogue
+  double owner_last_ns;   // owner fixup as the CTA's last item: peers' spill + first partial
+  double owner_mid_ns;    // owner fixup followed by more work (mostly hidden)
+  double peer_extra_ns;   // each further peer partial of a last-item fixup
+  double spill_last_ns;   // peer spill as the CTA's last item
 };
 
+// Figures measured on GB300 (per-CTA timeline traces and config sweeps).
 ModelCoeffs model_coeffs(const Cfg &c) {
   ModelCoeffs m;
   if (c.fam == FAM_F32) {
-    m = {1700.0, 500.0, 300.0, 1500.0, 300.0, 6000.0};
+    m = {1700.0, 500.0, 6000.0, 4000.0, 800.0, 1000.0, 2000.0};
   } else if (c.pair) {
-    m = {c.stages >= 6 ? 345.0 : 370.0, 400.0, 1000.0, 3000.0, 400.0, 10000.0};
+    m = {c.stages >= 6 ? 345.0 : 370.0, 400.0, 11500.0, 8000.0, 1000.0, 2500.0, 3000.0};
   } else if (c.BN == 256) {
-    m = {400.0, 300.0, 1000.0, 3000.0, 400.0, 9000.0};
+    m = {400.0, 300.0, 10000.0, 7000.0, 1000.0, 2000.0, 3000.0};
   } else {
-    m = {400.0, 250.0, 500.0, 2000.0, 250.0, 9000.0};
+    m = {400.0, 250.0, 10000.0, 5000.0, 800.0, 1500.0, 2000.0};
   }
   return m;
 }
@@ -370,6 +375,76 @@ double algorithmic_dram_bytes(const std::vector<Norm> &work) {
 }
 
 constexpr double kHbmBytesPerNs = 6500.0;   // measured copy bandwidth ~6.76 TB/s, rounded down
+constexpr double kL2ReuseBytes = 60e6;      // operand footprint that stays L2-resident (of 126 MB)
+
+// DRAM bytes the plan's operand loads are expected to cost.
+//  * DP tiles run in waves of g consecutive tiles that share A/B panels in
+//    L2: each wave reads the distinct row panels and column panels of its
+//    tiles once.
+//  * Stream-K units run far-apart parts of the tile list at the same time
+//    and share nothing while running; their k-slices come from DRAM unless
+//    all the SK tiles' panels fit in L2 together (then once each).
+// Output (and C_in) bytes are added for every tile.
+double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
+  const Sched &s = pl.s;
+  const double es = dtype_bytes(work[0].in_type);
+  auto panel_key = [](int32_t p, int32_t idx) { return ((uint64_t)(uint32_t)p << 32) | (uint32_t)idx; };
+  auto tile_of = [&](int64_t gt, int32_t &p, int32_t &tm, int32_t &tn) {
+    p = problem_of_tile(pl.ps.data(), s.num_problems, gt);
+    raster((int32_t)(gt - pl.ps[p].tile_base), pl.ps[p].tiles_m, pl.ps[p].tiles_n, tm, tn);
+  };
+  double bytes = 0;
+  // Stream-K part
+  if (s.sk_tiles > 0) {
+    std::vector<uint64_t> rows, cols;
+    double streamed_a = 0, streamed_b = 0;
+    for (int64_t t = 0; t < s.sk_tiles; ++t) {
+      int32_t p, tm, tn;
+      tile_of(t, p, tm, tn);
+      rows.push_back(panel_key(p, tm));
+      cols.push_back(panel_key(p, tn));
+      streamed_a += (double)pl.ps[p].iters * c.BK * c.BM * es;
+      streamed_b += (double)pl.ps[p].iters * c.BK * c.BN * es;
+    }
+    std::sort(rows.begin(), rows.end());
+    rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    double unique_a = 0, unique_b = 0;
+    for (uint64_t r : rows) unique_a += (double)c.BM * work[r >> 32].K * es;
+    for (uint64_t q : cols) unique_b += (double)c.BN * work[q >> 32].K * es;
+    if (unique_a + unique_b <= kL2ReuseBytes) {
+      bytes += unique_a + unique_b;
+    } else {
+      // an operand whose panels fit in half the budget stays resident
+      bytes += unique_a <= kL2ReuseBytes / 2 ? unique_a : streamed_a;
+      bytes += unique_b <= kL2ReuseBytes / 2 ? unique_b : streamed_b;
+    }
+  }
+  // data-parallel waves
+  std::vector<uint64_t> rows, cols;
+  const int64_t dp = s.total_tiles - s.sk_tiles;
+  for (int64_t w0 = 0; w0 < dp; w0 += s.g) {
+    rows.clear();
+    cols.clear();
+    const int64_t w1 = std::min<int64_t>(dp, w0 + s.g);
+    for (int64_t j = w0; j < w1; ++j) {
+      int32_t p, tm, tn;
+      tile_of(s.sk_tiles + j, p, tm, tn);
+      rows.push_back(panel_key(p, tm));
+      cols.push_back(panel_key(p, tn));
+    }
+    std::sort(rows.begin(), rows.end());
+    rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    for (uint64_t r : rows) bytes += (double)c.BM * work[r >> 32].K * es;
+    for (uint64_t q : cols) bytes += (double)c.BN * work[q >> 32].K * es;
+  }
+  for (const Norm &n : work)
+    bytes += (double)n.M * n.N * dtype_bytes(n.c_type) * (n.beta != 0.f ? 2.0 : 1.0);
+  return bytes;
+}
 
 double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
   const ModelCoeffs k = model_coeffs(c);
@@ -380,13 +455,16 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
     Item w;
     double t = 0;
     while (pl.s.num_problems > 0 && cursor_next(pl.s, pl.ps.data(), u, cur, w)) {
+      const bool last = cur.it >= cur.end && cur.dp >= pl.s.total_tiles;
       t += (w.k1 - w.k0) * k.iter_ns + k.item_ns;
-      if (w.role == ROLE_OWNER) t += k.owner_ns + (w.peer_last - w.peer_first) * k.peer_ns;
-      if (w.role == ROLE_PEER) t += k.spill_ns;
+      if (w.role == ROLE_OWNER)
+        t += last ? k.owner_last_ns + (w.peer_last - w.peer_first) * k.peer_extra_ns : k.owner_mid_ns;
+      if (w.role == ROLE_PEER && last) t += k.spill_last_ns;
     }
     crit = std::max(crit, t);
   }
-  return k.launch_ns + std::max(crit, algorithmic_dram_bytes(work) / kHbmBytesPerNs);
+  const double dram = std::max(algorithmic_dram_bytes(work), plan_dram_bytes(work, pl, c));
+  return k.launch_ns + std::max(crit, dram / kHbmBytesPerNs);
 }
 
 // --------------------------------------------------------------- launches
