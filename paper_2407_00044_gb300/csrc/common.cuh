@@ -55,6 +55,8 @@ enum InKind : int { IN_BF16 = 0, IN_E4M3 = 1 };
 struct TcProblem {
   CUtensorMap tmap_a;   // K-major: box {BK, 128}; MN-major: box {64, BK}
   CUtensorMap tmap_b;   // K-major: box {BK, BN};  MN-major: box {64, BK}
+  int32_t c_tma;        // epilogue writes C with TMA stores via TcParams::tmap_c
+  int32_t pad_;
   void *C;
   const void *C_in;
   int64_t ldc;          // C row-major
@@ -65,9 +67,12 @@ struct TcProblem {
   const float *scale_a, *scale_b;   // E4M3 per-tensor scales (may be null)
 };
 
+// The C tensor map serves single-problem launches only (c_tma is never set
+// in grouped ones): 64 more maps would exceed the 32 KB parameter limit.
 template <int MAXP>
 struct TcParams {
   TcProblem prob[MAXP];
+  CUtensorMap tmap_c[1];   // C of problem 0 (row-major, box {128 B of columns, 32 rows}, 128B swizzle)
   ProbSched ps[MAXP];
   Sched sched;
   Workspace ws;
@@ -92,9 +97,13 @@ __device__ __forceinline__ void trace_put(uint64_t *trace, int entry, uint32_t e
 // 120 KB, so two CTAs can never share an SM: each CTA holds up to all 512
 // TMEM columns, and an owner CTA waits on peer CTAs, so a peer stuck in
 // tcgen05.alloc behind its owner on the same SM would stall until timeout.
+// Epilogue staging for TMA stores of C: per epilogue warp two 4 KB buffers
+// (32 rows x 128 bytes, 128-byte swizzled).
+constexpr int EPI_STAGE_BYTES = 4 * 2 * 4096;
+
 inline int tc_smem_bytes(int bn, int stages) {
   const int stage = 128 * 128 + bn * 128;
-  const int need = 1024 /*alignment slack*/ + stages * stage + 512 /*barriers, TMEM slot*/;
+  const int need = 1024 /*alignment slack*/ + stages * stage + EPI_STAGE_BYTES + 512 /*barriers, TMEM slot*/;
   return need < 120 * 1024 ? 120 * 1024 : need;
 }
 

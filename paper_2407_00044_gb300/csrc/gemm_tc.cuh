@@ -147,7 +147,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   const uint32_t raw_addr = smem_u32(smem_raw);
   uint8_t *smem = smem_raw + ((1024u - (raw_addr & 1023u)) & 1023u);
   const int stages = P.stages;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + stages * STAGE_BYTES);
+  // [operand ring: stages x STAGE_BYTES][epilogue staging][barriers, TMEM slot]
+  uint8_t *epi_stage = smem + stages * STAGE_BYTES;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(epi_stage + EPI_STAGE_BYTES);
   uint64_t *full_bar = bars;
   uint64_t *empty_bar = bars + stages;
   uint64_t *tfull_bar = bars + 2 * stages;
@@ -375,6 +377,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     const int q4 = warp & 3;                 // TMEM lane quarter this warp may access
     const int row = q4 * 32 + lane;          // accumulator row of this thread
     const int et = threadIdx.x - 64;         // 0..127
+    // TMA-store staging of this warp: two 4 KB buffers of 32 rows x 128 B,
+    // 128-byte swizzled (16-byte chunk c of row r at chunk c ^ (r % 8)).
+    uint8_t *const my_stage = epi_stage + (warp - 2) * 8192;
+    int sbuf = 0;
     float4 *slots = reinterpret_cast<float4 *>(P.ws.partials);
     constexpr int64_t SLOT_F4 = (int64_t)128 * BN / 4;
     int acc = 0;
@@ -453,8 +459,46 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           if (pr.scale_b) alpha *= *pr.scale_b;
         }
         const int grow = w.tm * BM + (int)rank * 128 + row;
+        const int row0 = w.tm * BM + (int)rank * 128 + q4 * 32;   // first row of this warp
         auto store_chunk = [&](int ch, const float (&v)[32]) {
-          if (grow < pr.M) {
+          if (pr.c_tma) {
+            // Stage the chunk in shared memory and write it with one TMA
+            // store per 128-byte-wide box (BF16: 64 columns = two chunks;
+            // FP32: 32 columns); TMA clips rows/columns outside C.
+            constexpr bool F32OUT = sizeof(OutT) == 4;
+            const int part = F32OUT ? 0 : (ch & 1);
+            uint8_t *buf = my_stage + sbuf * 4096;
+            if (part == 0) {
+              if (lane == 0) bulk_wait_group_read<1>();   // this buffer's previous store has read it
+              __syncwarp();
+            }
+            uint8_t *rowp = buf + lane * 128;
+            if constexpr (F32OUT) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<float4 *>(rowp + ((q ^ (lane & 7)) * 16)) =
+                    make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2], alpha * v[4 * q + 3]);
+            } else {
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                uint4 pk;
+                __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                  h[e] = __floats2bfloat162_rn(alpha * v[8 * q + 2 * e], alpha * v[8 * q + 2 * e + 1]);
+                *reinterpret_cast<uint4 *>(rowp + (((part * 4 + q) ^ (lane & 7)) * 16)) = pk;
+              }
+            }
+            if (F32OUT || part == 1) {
+              fence_proxy_async_smem_cta();
+              __syncwarp();
+              if (lane == 0) {
+                tma_store_2d(&P.tmap_c[0], smem_u32(buf), w.tn * BN + (ch - part) * 32, row0);
+                bulk_commit_group();
+              }
+              sbuf ^= 1;
+            }
+          } else if (grow < pr.M) {
             const int gcol = w.tn * BN + ch * 32;
             if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
           }
@@ -550,6 +594,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         acc_phase ^= 1u;
       }
     }
+    // Every TMA store of this warp must finish before the CTA exits.
+    if (lane == 0) bulk_wait_group<0>();
+    __syncwarp();
   }
 
   tc_fence_before();

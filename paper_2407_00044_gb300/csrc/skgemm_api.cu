@@ -216,7 +216,7 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
     if (r.pair && r.BN != 256) return SK_ERR_UNSUPPORTED;
     r.BK = fam == FAM_BF16 ? 64 : 128;
     const int stage_bytes = 128 * 128 + (r.pair ? r.BN / 2 : r.BN) * 128;   // per CTA
-    const int max_stages = std::min(6, (227 * 1024 - 1024 - 512) / stage_bytes);
+    const int max_stages = std::min(6, (227 * 1024 - 1024 - 512 - EPI_STAGE_BYTES) / stage_bytes);
     r.stages = d.stages ? d.stages : max_stages;
     if (r.stages < 2 || r.stages > max_stages) return SK_ERR_UNSUPPORTED;
   }
@@ -514,6 +514,8 @@ sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk
   return SK_OK;
 }
 
+static_assert(sizeof(TcParams<MAXP_GROUPED>) <= 32000, "kernel parameter block too large");
+
 template <int MAXP>
 sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, const Cfg &c, Workspace ws,
                            cudaStream_t st) {
@@ -539,6 +541,21 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
     tp.C = n.C;
     tp.C_in = n.C_in;
     tp.ldc = n.ldc;
+    {
+      // TMA stores of C: beta == 0, 16-byte aligned base and row pitch.
+      const int ces = n.c_type == SK_F32 ? 4 : 2;
+      tp.c_tma = MAXP == 1 && n.beta == 0.f && aligned16(n.C) && (n.ldc * ces) % 16 == 0;
+      if (tp.c_tma) {
+        cuuint64_t dims[2] = {(cuuint64_t)n.N, (cuuint64_t)n.M};
+        cuuint64_t strides[1] = {(cuuint64_t)n.ldc * ces};
+        cuuint32_t box[2] = {(cuuint32_t)(128 / ces), 32};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = enc(&P->tmap_c[0], n.c_type == SK_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                         2, n.C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) tp.c_tma = 0;   // fall back to plain stores
+      }
+    }
     tp.M = (int32_t)n.M;
     tp.N = (int32_t)n.N;
     tp.K = (int32_t)n.K;
