@@ -83,7 +83,7 @@ struct TcParams {
 };
 
 constexpr int TRACE_ENTRIES = 128;
-constexpr int TRACE_MMA_BASE = 0, TRACE_EPI_BASE = 48, TRACE_CTA_BASE = 112;
+constexpr int TRACE_MMA_BASE = 0, TRACE_EPI_BASE = 48, TRACE_CTA_BASE = 112, TRACE_FIX_BASE = 116;
 
 __device__ __forceinline__ void trace_put(uint64_t *trace, int entry, uint32_t ev, uint32_t item, uint64_t t) {
   if (trace && entry >= 0 && entry < TRACE_ENTRIES) {

@@ -425,7 +425,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             __stcg(slot + (ch * 8 + j) * 128 + row, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         }
         release_acc(acc);
+        if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 4, 14, nitem, globaltimer_ordered());   // spill issued
         __threadfence();
+        if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // spill visible
         named_bar_sync(1, 128);
         if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + slot_id, 1u);
         if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
@@ -526,6 +528,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           int group = 0;
           for (int g0 = 0; g0 < nunits && ok; g0 += nb, ++group) {
             const int gn = nunits - g0 < nb ? nunits - g0 : nb;
+            if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
             if (et == 0) {
               fence_proxy_async_all();   // the acquired partials, to the copy engine
               for (int b = 0; b < gn; ++b) {
@@ -547,6 +550,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                 ok = false;
                 break;
               }
+              if (tr_lead && group == 0 && b == 0) trace_put(trace, TRACE_FIX_BASE + 1, 12, nitem, globaltimer_ordered());
+              if (tr_lead && group == 0 && b == gn - 1) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
               if (pi == 0) tmem_ld32(tbase + ch * 32, v);
               const float4 *sb = reinterpret_cast<const float4 *>(smem + b * FIX_UNIT_BYTES);
 #pragma unroll
