@@ -130,6 +130,9 @@ typedef struct {
                                 ignored elsewhere):
                                 each CTA records its timeline there, see
                                 SK_TRACE_* below; NULL = no tracing */
+    int raster_group;        /* tile rows walked together by the rasterisation
+                                (L2 locality of concurrently running tiles);
+                                0 = default 8, at most 64 */
 } sk_config;
 
 /* Timeline trace layout: CTA c owns entries [c*SK_TRACE_ENTRIES,

@@ -29,6 +29,7 @@ class Config:
     timeout_ns: int = 0
     debug_flags: int = 0
     trace: int = 0          # device pointer of a timeline buffer (see trace_gemm)
+    raster_group: int = 0   # rasterisation group in tile rows (0 = default)
 
     def to_c(self) -> B.sk_config:
         c = B.sk_config()
@@ -41,6 +42,7 @@ class Config:
         c.timeout_ns = self.timeout_ns
         c.debug_flags = self.debug_flags
         c.trace = self.trace or None
+        c.raster_group = self.raster_group
         return c
 
 

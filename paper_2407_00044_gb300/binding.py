@@ -49,7 +49,7 @@ class sk_config(ctypes.Structure):
         ("tile_m", ctypes.c_int), ("tile_n", ctypes.c_int), ("stages", ctypes.c_int),
         ("mode", ctypes.c_int), ("num_ctas", ctypes.c_int),
         ("min_iters_per_unit", ctypes.c_int), ("timeout_ns", ctypes.c_uint64),
-        ("debug_flags", ctypes.c_int), ("trace", ctypes.c_void_p),
+        ("debug_flags", ctypes.c_int), ("trace", ctypes.c_void_p), ("raster_group", ctypes.c_int),
     ]
 
 SK_TRACE_ENTRIES = 128

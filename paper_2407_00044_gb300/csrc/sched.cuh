@@ -29,10 +29,10 @@ namespace sk {
 
 enum : int32_t { ROLE_WHOLE = 0, ROLE_OWNER = 1, ROLE_PEER = 2, ROLE_DP = 3 };
 
-// Tile-row group size of the rasterisation: GROUP_M consecutive tile rows are
-// walked column by column so that CTAs running at the same time share A and
-// B panels in L2.
-constexpr int32_t GROUP_M = 8;
+// Default tile-row group of the rasterisation: group_m consecutive tile rows
+// are walked column by column so that CTAs running at the same time share A
+// and B panels in L2.
+constexpr int32_t GROUP_M_DEFAULT = 8;
 
 struct ProbSched {
   int32_t tiles_m, tiles_n;   // tile grid of the problem
@@ -47,6 +47,8 @@ struct Sched {
   int32_t g;                  // persistent CTAs (units)
   int32_t sk_units;           // CTAs with a Stream-K range (<= g)
   int32_t r;                  // sk_iters mod sk_units
+  int32_t group_m;            // rasterisation group (tile rows), >= 1
+  int32_t pad_;
   int64_t q;                  // sk_iters / sk_units
   int64_t total_tiles;
   int64_t sk_tiles;
@@ -97,12 +99,12 @@ SK_HD int32_t unit_of_iter(const Sched &s, int64_t it) {
   return (int32_t)(s.r + (it - big) / s.q);
 }
 
-SK_HD void raster(int32_t lt, int32_t tiles_m, int32_t tiles_n, int32_t &tm, int32_t &tn) {
-  int32_t per_group = GROUP_M * tiles_n;
+SK_HD void raster(int32_t lt, int32_t tiles_m, int32_t tiles_n, int32_t group_m, int32_t &tm, int32_t &tn) {
+  int32_t per_group = group_m * tiles_n;
   int32_t group = lt / per_group;
-  int32_t first_m = group * GROUP_M;
+  int32_t first_m = group * group_m;
   int32_t gm = tiles_m - first_m;
-  if (gm > GROUP_M) gm = GROUP_M;
+  if (gm > group_m) gm = group_m;
   int32_t in_group = lt - group * per_group;
   tm = first_m + in_group % gm;
   tn = in_group / gm;
@@ -161,7 +163,7 @@ SK_HD bool cursor_next(const Sched &s, const ProbSched *ps, int32_t u, Cursor &c
   }
   w.problem = p;
   w.tile = lt;
-  raster(lt, ps[p].tiles_m, ps[p].tiles_n, w.tm, w.tn);
+  raster(lt, ps[p].tiles_m, ps[p].tiles_n, s.group_m, w.tm, w.tn);
   w.pad_ = 0;
   return true;
 }

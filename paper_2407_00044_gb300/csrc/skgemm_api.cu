@@ -191,6 +191,7 @@ struct Cfg {
   uint64_t timeout_ns;
   int debug_flags;
   uint64_t *trace;
+  int raster_group;
   int ctas() const { return pair ? 2 * g : g; }
 };
 
@@ -232,6 +233,8 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.timeout_ns = d.timeout_ns ? d.timeout_ns : 2000000000ull;
   r.debug_flags = d.debug_flags;
   r.trace = d.trace;
+  if (d.raster_group < 0 || d.raster_group > 64) return SK_ERR_INVALID_ARG;
+  r.raster_group = d.raster_group ? d.raster_group : GROUP_M_DEFAULT;
   *out = r;
   return SK_OK;
 }
@@ -298,6 +301,8 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
   Sched &s = out->s;
   s.num_problems = (int32_t)out->ps.size();
   s.g = c.g;
+  s.group_m = c.raster_group;
+  s.pad_ = 0;
   s.total_tiles = tiles;
   s.sk_tiles = count_sk_tiles(tiles, c.g, c.mode);
   // iterations of the leading sk_tiles tiles
@@ -391,7 +396,7 @@ double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const C
   auto panel_key = [](int32_t p, int32_t idx) { return ((uint64_t)(uint32_t)p << 32) | (uint32_t)idx; };
   auto tile_of = [&](int64_t gt, int32_t &p, int32_t &tm, int32_t &tn) {
     p = problem_of_tile(pl.ps.data(), s.num_problems, gt);
-    raster((int32_t)(gt - pl.ps[p].tile_base), pl.ps[p].tiles_m, pl.ps[p].tiles_n, tm, tn);
+    raster((int32_t)(gt - pl.ps[p].tile_base), pl.ps[p].tiles_m, pl.ps[p].tiles_n, s.group_m, tm, tn);
   };
   double bytes = 0;
   // Stream-K part
@@ -673,8 +678,8 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   std::string key;
   {
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n, d->stages,
-                  (int)d->mode, d->num_ctas, d->min_iters_per_unit);
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n, d->stages,
+                  (int)d->mode, d->num_ctas, d->min_iters_per_unit, d->raster_group);
     key = buf;
     for (const Norm &n : work) {
       std::snprintf(buf, sizeof(buf), "%lld,%lld,%lld,%d,%d,%d,%d;", (long long)n.M, (long long)n.N,

@@ -214,3 +214,24 @@ def test_host_scheduler_unit_count_sweep(sk):
     for g in range(1, 153):
         _compare(sk, [(384, 384, 2048)], "sk", g, dtype="f32")
         _compare(sk, [(480, 512, 512)], "hybrid2", g)
+
+
+@pytest.mark.parametrize("group", [1, 3, 8, 16, 64])
+def test_raster_group_is_a_bijection(sk, group):
+    """Any rasterisation group keeps the schedule identical to the simulator
+    (tile indices) and maps tile indices one-to-one onto the tile grid."""
+    B = sk.binding
+    for shape in [(3840, 4096, 4096), (8192, 8192, 8192), (300, 2000, 700)]:
+        _compare(sk, [shape], "hybrid2", 152, tile_m=256)
+        cfg = {"mode": "dp", "raster_group": group, "tile_m": 128}
+        probs = [sk.shape_problem(*shape)]
+        info = sk.plan(probs, sk.Config(**cfg), num_sms=152)
+        seen = set()
+        for u in range(info.num_ctas):
+            for w in sk.unit_items(probs, u, config=sk.Config(**cfg), num_sms=152):
+                seen.add((w.tile_row, w.tile_col))
+        tm = -(-shape[0] // info.tile_m)
+        tn = -(-shape[1] // info.tile_n)
+        assert seen == {(i, j) for i in range(tm) for j in range(tn)}
+    bad = sk.shape_problem(64, 64, 64)
+    assert _q(sk, bad, {"raster_group": 65})[0] == B.SK_ERR_INVALID_ARG
