@@ -110,9 +110,8 @@ typedef struct {
 typedef struct {
     int tile_m;              /* 128, or 256 = CTA-pair kernel (two CTAs of a cluster
                                 share one 256 x tile_n tile through tcgen05
-                                cta_group::2; BF16/E4M3 with A row-major and B
-                                column-major only); 0 = chosen by the library's
-                                runtime model */
+                                cta_group::2; BF16 and E4M3); 0 = chosen by the
+                                library's runtime model */
     int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (pair: 256); 0 = chosen
                                 by the library's runtime model */
     int stages;              /* smem pipeline depth (BF16/E4M3: 2..6; default by tile) */

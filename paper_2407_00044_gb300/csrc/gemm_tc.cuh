@@ -118,7 +118,8 @@ struct OutStore<__nv_bfloat16> {
 
 // PAIR = false: one CTA per unit, 128 x BN tile, tcgen05 cta_group::1.
 // PAIR = true : a cluster of two CTAs per unit, 256 x BN tile.  Each CTA
-//   TMA-loads its own 128 rows of A and its half (BN/2 rows) of B into its
+//   TMA-loads its own 128 rows of A and its half (BN/2 rows) of B (either
+//   operand K-major or MN-major) into its
 //   own shared memory; both loads complete on the leader CTA's `full`
 //   barrier; the leader's MMA warp issues tcgen05.mma.cta_group::2 (M=256),
 //   which reads both CTAs' operands and writes rows 0-127 of the tile into
@@ -226,6 +227,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         const TcProblem &pr = P.prob[w.problem];
         const int m0 = w.tm * BM + (int)rank * 128;
         const int n0 = w.tn * BN + (int)rank * B_ROWS;
+        // Both operands K-major is the common case: one load per operand,
+        // decided once per item (a per-load layout test in the pair loop
+        // measured 16 % slower on 8192^3).
+        const bool kmaj = !(pr.a_mn | pr.b_mn);
         for (int kb = w.k0; kb < w.k1; ++kb) {
           if (!mbar_wait(smem_u32(empty_bar + stage), phase ^ 1u, tmo) || *abort_flag) {
             ok = false;
@@ -238,22 +243,44 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           const int kx = kb * BK;
           if constexpr (PAIR) {
             const uint32_t fbl = mapa_shared(fb, 0);   // the leader's barrier
-            tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
-            tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
-          } else {
-            if (!pr.a_mn) {
-              tma_load_2d(sa, &pr.tmap_a, fb, kx, m0);
+            if (kmaj) {
+              tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
+              tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
             } else {
+              if (!pr.a_mn) {
+                tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
+              } else {
 #pragma unroll
-              for (int ch = 0; ch < 128 / 64; ++ch)
-                tma_load_2d(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fb, m0 + 64 * ch, kx);
+                for (int ch = 0; ch < 128 / 64; ++ch)
+                  tma_load_2d_pair(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fbl, m0 + 64 * ch, kx);
+              }
+              if (!pr.b_mn) {
+                tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
+              } else {
+#pragma unroll
+                for (int ch = 0; ch < B_ROWS / 64; ++ch)
+                  tma_load_2d_pair(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fbl, n0 + 64 * ch, kx);
+              }
             }
-            if (!pr.b_mn) {
+          } else {
+            if (kmaj) {
+              tma_load_2d(sa, &pr.tmap_a, fb, kx, m0);
               tma_load_2d(sb, &pr.tmap_b, fb, kx, n0);
             } else {
+              if (!pr.a_mn) {
+                tma_load_2d(sa, &pr.tmap_a, fb, kx, m0);
+              } else {
 #pragma unroll
-              for (int ch = 0; ch < BN / 64; ++ch)
-                tma_load_2d(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fb, n0 + 64 * ch, kx);
+                for (int ch = 0; ch < 128 / 64; ++ch)
+                  tma_load_2d(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fb, m0 + 64 * ch, kx);
+              }
+              if (!pr.b_mn) {
+                tma_load_2d(sb, &pr.tmap_b, fb, kx, n0);
+              } else {
+#pragma unroll
+                for (int ch = 0; ch < BN / 64; ++ch)
+                  tma_load_2d(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fb, n0 + 64 * ch, kx);
+              }
             }
           }
           ++loads;
@@ -304,6 +331,14 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
         const TcProblem &pr = P.prob[w.problem];
         const uint32_t idesc = IDESC | ((uint32_t)pr.a_mn << 15) | ((uint32_t)pr.b_mn << 16);
+        // Operand descriptors of stage 0, k-step 0; a stage / k-step offset is
+        // added to the 14-bit start-address field (addresses < 256 KB, so the
+        // field cannot carry).  K-major: UMMA_K advances 32 bytes along the
+        // swizzled row; MN-major: UMMA_K rows of 128 bytes.
+        const uint64_t a_desc0 = smem_desc_sw128(tiles_addr, pr.a_mn ? MN_CHUNK_BYTES : 16, 1024);
+        const uint64_t b_desc0 = smem_desc_sw128(tiles_addr + A_BYTES, pr.b_mn ? MN_CHUNK_BYTES : 16, 1024);
+        const uint32_t a_kstep = pr.a_mn ? (UMMA_K * 128) >> 4 : 32 >> 4;
+        const uint32_t b_kstep = pr.b_mn ? (UMMA_K * 128) >> 4 : 32 >> 4;
         const int tr = TRACE_MMA_BASE + 3 * nitem;
         const bool got = PAIR ? mbar_wait_cluster(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo)
                               : mbar_wait(smem_u32(tempty_bar + acc), acc_phase ^ 1u, tmo);
@@ -320,16 +355,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             break;
           }
           tc_fence_after();
-          const uint32_t sa = tiles_addr + stage * STAGE_BYTES;
-          const uint32_t sb = sa + A_BYTES;
+          const uint64_t soff = (uint64_t)((stage * STAGE_BYTES) >> 4);
 #pragma unroll
           for (int kk = 0; kk < BK / UMMA_K; ++kk) {
-            // K-major: advance 32 bytes along the swizzled row per UMMA_K;
-            // MN-major: advance UMMA_K rows of 128 bytes.
-            const uint64_t ad = pr.a_mn ? smem_desc_sw128(sa + kk * UMMA_K * 128, MN_CHUNK_BYTES, 1024)
-                                        : smem_desc_sw128(sa + kk * 32, 16, 1024);
-            const uint64_t bd = pr.b_mn ? smem_desc_sw128(sb + kk * UMMA_K * 128, MN_CHUNK_BYTES, 1024)
-                                        : smem_desc_sw128(sb + kk * 32, 16, 1024);
+            const uint64_t ad = a_desc0 + soff + (uint64_t)(kk * a_kstep);
+            const uint64_t bd = b_desc0 + soff + (uint64_t)(kk * b_kstep);
             const uint32_t accum = (kb > w.k0 || kk > 0) ? 1u : 0u;
             if constexpr (PAIR) {
               if constexpr (IN == IN_BF16)

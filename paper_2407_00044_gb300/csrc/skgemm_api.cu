@@ -487,8 +487,11 @@ sk_status check_tc_alignment(const Norm &n) {
   return SK_OK;
 }
 
+// The pair kernel reads MN-major (transposed) BF16 operands too; E4M3 is
+// K-major only (checked by check_tc_alignment).
 sk_status check_pair_layout(const Norm &n) {
-  return (n.a_layout == SK_ROW_MAJOR && n.b_layout == SK_COL_MAJOR) ? SK_OK : SK_ERR_UNSUPPORTED;
+  (void)n;
+  return SK_OK;
 }
 
 sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk_dtype t, bool kmajor, int64_t rows,
@@ -705,9 +708,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
       return SK_OK;
     }
   }
-  bool pair_ok = fam != FAM_F32 && (d->num_ctas > 0 ? d->num_ctas : sms) >= 2;
-  for (const Norm &n : work)
-    if (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR) pair_ok = false;
+  const bool pair_ok = fam != FAM_F32 && (d->num_ctas > 0 ? d->num_ctas : sms) >= 2;
   std::vector<int> tms, tns;
   std::vector<sk_mode> modes;
   if (free_tile_m) {

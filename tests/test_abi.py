@@ -192,13 +192,15 @@ def test_tile_selection(sk):
     # K-major operands and m >= 256: CTA pairs with 256 x 256 tiles
     info = _q(sk, sk.shape_problem(3840, 4096, 4096))[1]
     assert (info.tile_m, info.tile_n, info.num_ctas) == (256, 256, 74)
-    # m < 256, transposed operands, or FP32: 128-row tiles on every CTA
-    for p in (sk.shape_problem(128, 8192, 16384), sk.shape_problem(4096, 4096, 4096, a_layout="col"),
-              sk.shape_problem(384, 384, 2048, dtype="f32")):
+    # m <= 128 (memory-bound) or FP32: 128-row tiles on every CTA
+    for p in (sk.shape_problem(128, 8192, 16384), sk.shape_problem(384, 384, 2048, dtype="f32")):
         info = _q(sk, p)[1]
         assert (info.tile_m, info.num_ctas) == (128, 148)
-    # asking for pairs with transposed operands is refused
-    assert _q(sk, sk.shape_problem(4096, 4096, 4096, b_layout="row"), {"tile_m": 256})[0] == B.SK_ERR_UNSUPPORTED
+    # transposed (MN-major) BF16 operands may use pairs
+    assert _q(sk, sk.shape_problem(4096, 4096, 4096, b_layout="row"), {"tile_m": 256})[0] == B.SK_OK
+    # E4M3 transposed operands are refused by either kernel
+    assert _q(sk, sk.shape_problem(4096, 4096, 4096, dtype="e4m3", b_layout="row"), {"tile_m": 256})[0] == \
+        B.SK_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("tile_m", [128, 256])

@@ -126,17 +126,19 @@ def test_bf16_beta(m):
     assert np.all(np.abs(to_np(out) - ref) <= tol)
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("al,bl,cl", [("col", "col", "row"), ("row", "row", "row"),
                                       ("col", "row", "row"), ("row", "col", "col"),
                                       ("col", "row", "col")])
-def test_bf16_transposed_layouts(m, al, bl, cl):
-    """MN-major operands (A column-major / B row-major) and column-major C."""
+def test_bf16_transposed_layouts(m, al, bl, cl, tile_m):
+    """MN-major operands (A column-major / B row-major) and column-major C,
+    on the single-CTA and the CTA-pair kernel."""
     M, N, K = 328, 272, 648   # multiples of 8: 16-byte leading dimensions for TMA
     a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", a_layout=al, b_layout=bl, seed=10, dist="int")
     d = dev()
     out = workloads.as_layout(torch.empty(M, N, dtype=torch.float32), cl)
     out = torch.empty_strided(out.shape, out.stride(), dtype=torch.float32, device=d)
-    m.gemm(same_strides(a, d), same_strides(b, d), out, config=m.Config(mode="sk"))
+    m.gemm(same_strides(a, d), same_strides(b, d), out, config=m.Config(mode="sk", tile_m=tile_m))
     assert m.default_workspace(d).status() == 0
     ref, _ = oracle.gemm(a, b)
     assert np.array_equal(to_np(out), ref), (al, bl, cl)

@@ -97,14 +97,15 @@ def test_backward_fd_shape(m):
     assert dA.stride() == a.stride() and dB.stride() == b.stride()
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("al,bl", [("row", "col"), ("row", "row"), ("col", "col"), ("col", "row")])
-def test_backward_layouts_exact(m, al, bl):
+def test_backward_layouts_exact(m, al, bl, tile_m):
     M, N, K = 264, 392, 520
     d = dev()
     a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", a_layout=al, b_layout=bl, seed=52, dist="int")
     g = workloads.small_int((M, N), seed=53).to(torch.bfloat16)
     from gpu_common import same_strides
-    dA, dB = m.gemm_backward(same_strides(a, d), same_strides(b, d), g.to(d))
+    dA, dB = m.gemm_backward(same_strides(a, d), same_strides(b, d), g.to(d), config=m.Config(tile_m=tile_m))
     rA, _ = oracle.gemm(g, b.t())
     rB, _ = oracle.gemm(a.t(), g)
     # exact integers that fit BF16 output: |values| <= 4 * 392 < 2^8? not in
