@@ -24,9 +24,12 @@ def test_candidates_ranked_and_valid(sk):
     assert preds == sorted(preds) and preds[0] > 0
     tiles = {(cfg.tile_m, cfg.tile_n) for cfg, _ in c}
     assert tiles == {(128, 128), (128, 256), (256, 256)}
-    # transposed A: no CTA-pair candidates
+    # transposed A: the CTA pair reads MN-major operands too
     p = sk.shape_problem(4096, 4096, 4096, a_layout="col")
-    assert all(cfg.tile_m == 128 for cfg, _ in sk.autotune.candidates(p, num_sms=152))
+    assert {cfg.tile_m for cfg, _ in sk.autotune.candidates(p, num_sms=152)} == {128, 256}
+    # transposed E4M3 operands are refused by both kernels: no candidates
+    p = sk.shape_problem(4096, 4096, 4096, dtype="e4m3", a_layout="col")
+    assert sk.autotune.candidates(p, num_sms=152) == []
     # FP32: one tile
     p = sk.shape_problem(384, 384, 2048, dtype="f32")
     assert {(cfg.tile_m, cfg.tile_n) for cfg, _ in sk.autotune.candidates(p, num_sms=152)} == {(128, 128)}
