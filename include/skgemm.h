@@ -106,6 +106,20 @@ typedef struct {
     const float *scale_b;
 } sk_problem;
 
+/* How a tile split across units gets its partial sums added (Stream-K's
+ * "fixup", Background and Methodology sections).  Both orders of addition are
+ * the same -- the partial of the unit holding k-block 0 first, then the other
+ * units' partials by ascending unit index -- so both give bit-identical C. */
+typedef enum {
+    SK_FIXUP_OWNER = 0,        /* the unit holding k-block 0 waits (bounded) for
+                                  the others' flags and adds their partials */
+    SK_FIXUP_LAST_ARRIVER = 1  /* every contributor spills its partial and counts
+                                  its arrival with one atomic; the contributor that
+                                  completes the count adds all partials.  No unit
+                                  ever waits; the workspace holds twice the partial
+                                  slots (no counterpart in the paper) */
+} sk_fixup;
+
 /* Launch configuration.  Zero in any field selects the default. */
 typedef struct {
     int tile_m;              /* 128, or 256 = CTA-pair kernel (two CTAs of a cluster
@@ -132,6 +146,7 @@ typedef struct {
     int raster_group;        /* tile rows walked together by the rasterisation
                                 (L2 locality of concurrently running tiles);
                                 0 = default 8, at most 64 */
+    sk_fixup fixup;          /* partial-sum fixup protocol; default SK_FIXUP_OWNER */
 } sk_config;
 
 /* Timeline trace layout: CTA c owns entries [c*SK_TRACE_ENTRIES,

@@ -30,6 +30,7 @@ class Config:
     debug_flags: int = 0
     trace: int = 0          # device pointer of a timeline buffer (see trace_gemm)
     raster_group: int = 0   # rasterisation group in tile rows (0 = default)
+    fixup: str = "owner"    # "owner" (owner waits for peers) or "last_arriver"
 
     def to_c(self) -> B.sk_config:
         c = B.sk_config()
@@ -43,6 +44,7 @@ class Config:
         c.debug_flags = self.debug_flags
         c.trace = self.trace or None
         c.raster_group = self.raster_group
+        c.fixup = B.FIXUP_NAMES[self.fixup] if isinstance(self.fixup, str) else int(self.fixup)
         return c
 
 
@@ -104,15 +106,21 @@ def make_problem(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor, *, C_in=Non
     return p
 
 
+def default_workspace_bytes(sms: int) -> int:
+    """Workspace for any call on a GPU with ``sms`` SMs: status word, one
+    flag per CTA, and two 128 x 256 FP32 slots per CTA (the second is used by
+    the last-arriver fixup only)."""
+    return 256 + (-(-sms * 4 // 256)) * 256 + 2 * sms * 128 * 256 * 4
+
+
 class Workspace:
     """A zero-initialised device buffer large enough for any call on one
-    device (sized for the largest tile and every SM)."""
+    device (sized for the largest tile, every SM and either fixup)."""
 
     def __init__(self, device=None, nbytes: int | None = None):
         self.device = torch.device(device if device is not None else torch.cuda.current_device())
         if nbytes is None:
-            sms = torch.cuda.get_device_properties(self.device).multi_processor_count
-            nbytes = 256 + (-(-sms * 4 // 256)) * 256 + sms * 128 * 256 * 4
+            nbytes = default_workspace_bytes(torch.cuda.get_device_properties(self.device).multi_processor_count)
         self.nbytes = int(nbytes)
         self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=self.device)
         with torch.cuda.device(self.device):

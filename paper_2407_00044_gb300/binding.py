@@ -50,7 +50,11 @@ class sk_config(ctypes.Structure):
         ("mode", ctypes.c_int), ("num_ctas", ctypes.c_int),
         ("min_iters_per_unit", ctypes.c_int), ("timeout_ns", ctypes.c_uint64),
         ("debug_flags", ctypes.c_int), ("trace", ctypes.c_void_p), ("raster_group", ctypes.c_int),
+        ("fixup", ctypes.c_int),
     ]
+
+SK_FIXUP_OWNER, SK_FIXUP_LAST_ARRIVER = 0, 1
+FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER}
 
 SK_TRACE_ENTRIES = 128
 SK_TRACE_BYTES_PER_CTA = SK_TRACE_ENTRIES * 16

@@ -14,10 +14,15 @@ constexpr uint32_t STATUS_TIMEOUT = 4;  // == SK_ERR_TIMEOUT
 
 // Device views of the caller's workspace.
 struct Workspace {
-  float *partials;      // g slots of tile_m * tile_n floats
-  uint32_t *flags;      // g flags, zero between calls
-  uint32_t *status;     // 0, or STATUS_TIMEOUT after an expired wait
+  float *partials;        // g slots of tile_m * tile_n floats (a unit's peer segment)
+  uint32_t *flags;        // g flags (owner fixup) or arrival counters (last-arriver
+                          // fixup, indexed by the owner's slot), zero between calls
+  uint32_t *status;       // 0, or STATUS_TIMEOUT after an expired wait
+  float *owner_partials;  // last-arriver fixup: g more slots (a unit's owner segment)
 };
+
+// Fixup protocols (sk_fixup).
+constexpr int32_t FIXUP_OWNER = 0, FIXUP_LAST_ARRIVER = 1;
 
 // ----------------------------------------------------------- FP32 SIMT path
 constexpr int F32_BM = 128, F32_BN = 128, F32_BK = 16, F32_THREADS = 256;
@@ -47,6 +52,7 @@ struct SimtParams {
   Workspace ws;
   uint64_t timeout_ns;
   int32_t debug_flags;
+  int32_t fixup;
 };
 
 // --------------------------------------------------------- tcgen05 path
@@ -80,6 +86,8 @@ struct TcParams {
   int32_t stages;
   int32_t debug_flags;
   uint64_t *trace;      // optional per-CTA timeline (SK_TRACE_* in skgemm.h)
+  int32_t fixup;
+  int32_t pad_;
 };
 
 constexpr int TRACE_ENTRIES = 128;

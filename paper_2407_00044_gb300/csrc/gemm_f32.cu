@@ -8,6 +8,10 @@
 //   owner : waits for its peers' flags (bounded), adds their partials in
 //           ascending CTA order, then runs the epilogue
 //   whole / dp : runs the epilogue
+// With the last-arriver fixup, owner and peers both write their partials
+// and count their arrival at the owner's counter; the CTA completing the
+// count sums the partials in the same order (owner's, then peers
+// ascending) and runs the epilogue.  Nobody waits.
 // Epilogue: C = alpha * acc + beta * C_in, bounds-masked (no padding).
 // FP32 needs FFMA: TF32 tensor-core products would miss the 5e-5 relative
 // accuracy this path promises.
@@ -87,6 +91,9 @@ __device__ __forceinline__ void store_slice(float (*S)[F32_BM + PAD], int kmajor
 template <int MAXP>
 __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __grid_constant__ SimtParams<MAXP> P) {
   __shared__ __align__(16) F32Smem sm;
+  __shared__ uint32_t fix_word[2];   // last-arriver decisions, alternating
+  int ndecide = 0;
+  const bool last_arriver = P.fixup == FIXUP_LAST_ARRIVER;
   const int t = threadIdx.x;
   const int ty = t >> 4, tx = t & 15;
   const int u = blockIdx.x;
@@ -144,23 +151,82 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
     // Partial slot layout: float4 index v*256 + t, v = row_group*2 + col_half,
     // so consecutive threads touch consecutive 16-byte words.
     float4 *slot_base = reinterpret_cast<float4 *>(P.ws.partials);
+    float4 *oslot_base = reinterpret_cast<float4 *>(P.ws.owner_partials);
     const int64_t slot_f4 = (int64_t)F32_BM * F32_BN / 4;
-
-    if (w.role == ROLE_PEER) {
-      float4 *slot = slot_base + (int64_t)u * slot_f4;
+    auto spill = [&](float4 *slot) {
 #pragma unroll
       for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int h = 0; h < 2; ++h)
           __stcg(slot + (i * 2 + h) * F32_THREADS + t,
                  make_float4(acc[i][h * 4 + 0], acc[i][h * 4 + 1], acc[i][h * 4 + 2], acc[i][h * 4 + 3]));
+    };
+    // acc = slot (assign) or acc += slot.
+    auto gather = [&](const float4 *slot, bool assign) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 v = __ldcg(slot + (i * 2 + h) * F32_THREADS + t);
+          if (assign) {
+            acc[i][h * 4 + 0] = v.x;
+            acc[i][h * 4 + 1] = v.y;
+            acc[i][h * 4 + 2] = v.z;
+            acc[i][h * 4 + 3] = v.w;
+          } else {
+            acc[i][h * 4 + 0] += v.x;
+            acc[i][h * 4 + 1] += v.y;
+            acc[i][h * 4 + 2] += v.z;
+            acc[i][h * 4 + 3] += v.w;
+          }
+        }
+    };
+    auto broadcast = [&](bool mine) {
+      volatile uint32_t *word = fix_word + (ndecide++ & 1);
+      if (t == 0) *word = mine ? 1u : 0u;
+      cta_sync();
+      return *word != 0u;
+    };
+
+    if (w.role == ROLE_PEER) {
+      spill(slot_base + (int64_t)u * slot_f4);
       __threadfence();
       cta_sync();
-      if (t == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + u, 1u);
-      continue;
-    }
-
-    if (w.role == ROLE_OWNER) {
+      if (!last_arriver) {
+        if (t == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + u, 1u);
+        continue;
+      }
+      // Count this arrival at the tile's owner o; the CTA completing the
+      // count (pl - o earlier arrivals) sums the tile in the fixed order.
+      const ProbSched &q = P.ps[w.problem];
+      const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
+      const int o = unit_of_iter(S, ts);
+      const int pl = unit_of_iter(S, ts + q.iters - 1);
+      bool mine = false;
+      if (t == 0) mine = atom_add_acq_rel_gpu(P.ws.flags + o, 1u) == (uint32_t)(pl - o);
+      if (!broadcast(mine)) continue;
+      gather(oslot_base + (int64_t)o * slot_f4, true);
+      for (int p = o + 1; p <= pl; ++p) gather(slot_base + (int64_t)p * slot_f4, false);
+      if (t == 0) P.ws.flags[o] = 0u;
+    } else if (w.role == ROLE_OWNER && last_arriver) {
+      // If every peer has already arrived, sum now; otherwise write this
+      // partial to the owner slot and count this arrival too.
+      const uint32_t npeers = (uint32_t)(w.peer_last - w.peer_first + 1);
+      bool mine = false;
+      if (t == 0) {
+        mine = ld_relaxed_gpu(P.ws.flags + u) == npeers;
+        if (mine) fence_acq_rel_gpu();
+      }
+      if (!broadcast(mine)) {
+        spill(oslot_base + (int64_t)u * slot_f4);
+        __threadfence();
+        cta_sync();
+        if (t == 0) mine = atom_add_acq_rel_gpu(P.ws.flags + u, 1u) == npeers;
+        if (!broadcast(mine)) continue;
+      }
+      for (int p = w.peer_first; p <= w.peer_last; ++p) gather(slot_base + (int64_t)p * slot_f4, false);
+      if (t == 0) P.ws.flags[u] = 0u;
+    } else if (w.role == ROLE_OWNER) {
       if (t == 0) {
         // Relaxed polls of every peer flag overlap; one acquire fence then
         // orders the partial reads after the peers' release stores.
@@ -178,19 +244,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
       }
       cta_sync();
       // Fixed summation order: own partial, then peers in ascending CTA index.
-      for (int p = w.peer_first; p <= w.peer_last; ++p) {
-        const float4 *slot = slot_base + (int64_t)p * slot_f4;
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            float4 v = __ldcg(slot + (i * 2 + h) * F32_THREADS + t);
-            acc[i][h * 4 + 0] += v.x;
-            acc[i][h * 4 + 1] += v.y;
-            acc[i][h * 4 + 2] += v.z;
-            acc[i][h * 4 + 3] += v.w;
-          }
-      }
+      for (int p = w.peer_first; p <= w.peer_last; ++p) gather(slot_base + (int64_t)p * slot_f4, false);
       cta_sync();
       if (t == 0)
         for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[p] = 0u;

@@ -25,6 +25,7 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
 #include "common.cuh"
 #include "ptx.cuh"
 
@@ -159,6 +160,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fix_bar + FIX_SMEM_UNITS);
   volatile uint32_t *abort_flag = tmem_slot + 1;
+  volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
+  volatile uint32_t *fix_fail = tmem_slot + 4;   // two words: a staged-sum group failed
   const uint32_t tiles_addr = smem_u32(smem);
 
   const int warp = threadIdx.x >> 5;
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     mbar_init(smem_u32(done_bar), 1);
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
     *abort_flag = 0;
+    fix_fail[0] = fix_fail[1] = 0;
     fence_barrier_init();
     fence_proxy_async_smem();
   }
@@ -411,8 +415,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     // 128-byte swizzled (16-byte chunk c of row r at chunk c ^ (r % 8)).
     uint8_t *const my_stage = epi_stage + (warp - 2) * 8192;
     int sbuf = 0;
-    float4 *slots = reinterpret_cast<float4 *>(P.ws.partials);
+    float4 *const slots = reinterpret_cast<float4 *>(P.ws.partials);         // peer segments
+    float4 *const oslots = reinterpret_cast<float4 *>(P.ws.owner_partials);  // owner segments (last arriver)
     constexpr int64_t SLOT_F4 = (int64_t)128 * BN / 4;
+    const bool last_arriver = P.fixup == FIXUP_LAST_ARRIVER;
+    int ndecide = 0;   // last-arriver decisions so far; its parity picks the smem word
     int acc = 0;
     uint32_t acc_phase = 0;
     Cursor c;
@@ -429,23 +436,85 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           mbar_arrive(smem_u32(tempty_bar + a));
       }
     };
+    // Slot / flag / counter index of unit p's CTA holding these rows.
+    auto cslot = [&](int p) { return PAIR ? 2 * p + (int)rank : p; };
     int nitem = 0;
     const bool tr_lead = TRACE && et == 0;
-    // Loop exit and wait results are made warp-uniform: the lanes of an
-    // epilogue warp must stay converged for the warp-collective tcgen05.ld.
-    while (!__any_sync(0xffffffffu, *abort_flag != 0u) && cursor_next(S, P.ps, u, c, w)) {
+    // Loop exit and wait results are made uniform over the 128 epilogue
+    // threads: the lanes of a warp must stay converged for the
+    // warp-collective tcgen05.ld, and all four warps must reach the same
+    // named barriers.
+    while (cursor_next(S, P.ps, u, c, w)) {
       const TcProblem &pr = P.prob[w.problem];
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo))) {
-        fail();
+      const bool got = mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo);
+      if (named_bar_or(1, 128, !got || *abort_flag != 0u)) {
+        if (!got) fail();
         break;
       }
       tc_fence_after();
       const int tr = TRACE_EPI_BASE + 3 * nitem;
       if (tr_lead && nitem < 21) trace_put(trace, tr, 5, nitem, globaltimer_ordered());
       const uint32_t tbase = tmem_base + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(acc * BN);
+      // The item is this CTA's last: every MMA has completed, so the operand
+      // ring in shared memory is free for staging partials.
+      const bool ring_free = c.it >= c.end && c.dp >= S.total_tiles;
 
-      if (w.role == ROLE_PEER) {
-        float4 *slot = slots + (int64_t)slot_id * SLOT_F4;
+      auto get_alpha = [&]() {
+        float alpha = pr.alpha;
+        if (IN == IN_E4M3) {
+          if (pr.scale_a) alpha *= *pr.scale_a;
+          if (pr.scale_b) alpha *= *pr.scale_b;
+        }
+        return alpha;
+      };
+      const int grow = w.tm * BM + (int)rank * 128 + row;
+      const int row0 = w.tm * BM + (int)rank * 128 + q4 * 32;   // first row of this warp
+      auto store_chunk = [&](int ch, const float (&v)[32], float alpha) {
+        if (pr.c_tma) {
+          // Stage the chunk in shared memory and write it with one TMA
+          // store per 128-byte-wide box (BF16: 64 columns = two chunks;
+          // FP32: 32 columns); TMA clips rows/columns outside C.
+          constexpr bool F32OUT = sizeof(OutT) == 4;
+          const int part = F32OUT ? 0 : (ch & 1);
+          uint8_t *buf = my_stage + sbuf * 4096;
+          if (part == 0) {
+            if (lane == 0) bulk_wait_group_read<1>();   // this buffer's previous store has read it
+            __syncwarp();
+          }
+          uint8_t *rowp = buf + lane * 128;
+          if constexpr (F32OUT) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              *reinterpret_cast<float4 *>(rowp + ((q ^ (lane & 7)) * 16)) =
+                  make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2], alpha * v[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              uint4 pk;
+              __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                h[e] = __floats2bfloat162_rn(alpha * v[8 * q + 2 * e], alpha * v[8 * q + 2 * e + 1]);
+              *reinterpret_cast<uint4 *>(rowp + (((part * 4 + q) ^ (lane & 7)) * 16)) = pk;
+            }
+          }
+          if (F32OUT || part == 1) {
+            fence_proxy_async_smem_cta();
+            __syncwarp();
+            if (lane == 0) {
+              tma_store_2d(&P.tmap_c[0], smem_u32(buf), w.tn * BN + (ch - part) * 32, row0);
+              bulk_commit_group();
+            }
+            sbuf ^= 1;
+          }
+        } else if (grow < pr.M) {
+          const int gcol = w.tn * BN + ch * 32;
+          if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
+        }
+      };
+      // Writes this CTA's accumulator rows to a workspace slot, in TMEM
+      // fragment order: float4 (chunk*8 + j)*128 + row (coalesced per warp).
+      auto spill = [&](float4 *slot) {
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
           float v[32];
@@ -454,26 +523,167 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           for (int j = 0; j < 8; ++j)
             __stcg(slot + (ch * 8 + j) * 128 + row, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         }
+      };
+      // Sums the partials of a tile whose k-blocks units o..pl computed, in
+      // the fixed order: unit o's partial (k-block 0; from this CTA's TMEM
+      // if own_in_tmem, else from o's owner slot), then units o+1..pl
+      // ascending (their peer slots), and stores C.  Every partial has been
+      // acquired by the caller.  own_in_tmem is a compile-time constant: a
+      // run-time flag here measured 2 us slower on 128 x 8192 x 16384.
+      auto fixup_sum = [&](auto own_c, int o, int pl) {
+        constexpr bool own_in_tmem = decltype(own_c)::value;
+        const float alpha = get_alpha();
+        constexpr int NCH = BN / 32;
+        auto src_of = [&](int ch, int ti) -> const float4 * {
+          // ti-th staged term: own_in_tmem ? peer o+1+ti : (ti == 0 ? owner o : peer o+ti)
+          const float4 *base = own_in_tmem ? slots + (int64_t)cslot(o + 1 + ti) * SLOT_F4
+                               : ti == 0   ? oslots + (int64_t)cslot(o) * SLOT_F4
+                                           : slots + (int64_t)cslot(o + ti) * SLOT_F4;
+          return base + (ch * 8) * 128;
+        };
+        const int nst = (pl - o) + (own_in_tmem ? 0 : 1);   // terms read from the workspace
+        if (ring_free) {
+          // Stage the partials in the idle ring with bulk copies, 16 KB units
+          // (chunk, term) in chunk-major order, up to FIX_SMEM_UNITS in flight.
+          const int nunits = NCH * nst;
+          int nb = (stages * STAGE_BYTES) / FIX_UNIT_BYTES;
+          if (nb > FIX_SMEM_UNITS) nb = FIX_SMEM_UNITS;
+          float v[32];
+          int group = 0;
+          for (int g0 = 0; g0 < nunits; g0 += nb, ++group) {
+            const int gn = nunits - g0 < nb ? nunits - g0 : nb;
+            if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
+            if (et == 0) {
+              fence_proxy_async_all();   // the acquired partials, to the copy engine
+              for (int b = 0; b < gn; ++b) {
+                const int i = g0 + b;
+                const int ch = i / nst;
+                const uint32_t fb = smem_u32(fix_bar + b);
+                mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
+                bulk_copy_g2s(tiles_addr + b * FIX_UNIT_BYTES, src_of(ch, i - ch * nst), FIX_UNIT_BYTES, fb);
+              }
+            }
+            for (int b = 0; b < gn; ++b) {
+              const int i = g0 + b;
+              const int ch = i / nst;
+              const int ti = i - ch * nst;
+              if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(fix_bar + b), (uint32_t)(group & 1), tmo))) {
+                fail();
+                if (lane == 0) fix_fail[group & 1] = 1u;
+                break;
+              }
+              if (tr_lead && group == 0 && b == 0) trace_put(trace, TRACE_FIX_BASE + 1, 12, nitem, globaltimer_ordered());
+              if (tr_lead && group == 0 && b == gn - 1) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
+              const float4 *sb = reinterpret_cast<const float4 *>(smem + b * FIX_UNIT_BYTES);
+              if (ti == 0 && !own_in_tmem) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const float4 q = sb[j * 128 + row];
+                  v[4 * j] = q.x;
+                  v[4 * j + 1] = q.y;
+                  v[4 * j + 2] = q.z;
+                  v[4 * j + 3] = q.w;
+                }
+              } else {
+                if (ti == 0) tmem_ld32(tbase + ch * 32, v);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                  const float4 q = sb[j * 128 + row];
+                  v[4 * j] += q.x;
+                  v[4 * j + 1] += q.y;
+                  v[4 * j + 2] += q.z;
+                  v[4 * j + 3] += q.w;
+                }
+              }
+              if (ti == nst - 1) store_chunk(ch, v, alpha);
+            }
+            // Every thread is done with the group's buffers; a failed wait
+            // in any warp ends the sum in all of them.  (A group's failure
+            // word is written only before its barrier and, alternating by
+            // parity, not again before every thread has read it; a plain
+            // barrier here measured faster than a reducing one.)
+            named_bar_sync(1, 128);
+            if (fix_fail[group & 1] != 0u) break;
+          }
+        } else {
+          // More work follows on this CTA: the sum overlaps the next item's
+          // MMAs, so plain loads suffice.
+#pragma unroll 1
+          for (int ch = 0; ch < NCH; ++ch) {
+            float v[32];
+            if (own_in_tmem) {
+              tmem_ld32(tbase + ch * 32, v);
+            } else {
+              const float4 *src = src_of(ch, 0) + row;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 q = __ldcg(src + j * 128);
+                v[4 * j] = q.x;
+                v[4 * j + 1] = q.y;
+                v[4 * j + 2] = q.z;
+                v[4 * j + 3] = q.w;
+              }
+            }
+            for (int ti = own_in_tmem ? 0 : 1; ti < nst; ++ti) {
+              const float4 *src = src_of(ch, ti) + row;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 q = __ldcg(src + j * 128);
+                v[4 * j] += q.x;
+                v[4 * j + 1] += q.y;
+                v[4 * j + 2] += q.z;
+                v[4 * j + 3] += q.w;
+              }
+            }
+            store_chunk(ch, v, alpha);
+          }
+        }
+      };
+      // Last-arriver fixup: one thread's decision, broadcast to the 128
+      // epilogue threads through one of two shared words (alternating, so
+      // a word is rewritten only after every thread has read it).
+      auto broadcast = [&](bool mine) {
+        volatile uint32_t *word = fix_word + (ndecide++ & 1);
+        if (et == 0) *word = mine ? 1u : 0u;
+        named_bar_sync(1, 128);
+        return *word != 0u;
+      };
+
+      // Which sum, if any, this CTA does for the item: units o..pl's
+      // partials, the first from TMEM (own_tmem) or from o's owner slot.
+      bool do_sum = false, own_tmem = true;
+      int o = u, pl = w.peer_last;
+      if (w.role == ROLE_PEER) {
+        spill(slots + (int64_t)slot_id * SLOT_F4);
         release_acc(acc);
         if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 4, 14, nitem, globaltimer_ordered());   // spill issued
         __threadfence();
         if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // spill visible
         named_bar_sync(1, 128);
-        if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + slot_id, 1u);
-        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
-      } else {
-        // Peer units p hold their partial of this CTA's rows in slot
-        // (PAIR ? 2p + rank : p).
-        if (w.role == ROLE_OWNER) {
+        if (!last_arriver) {
+          if (et == 0 && !(P.debug_flags & DEBUG_SKIP_PEER_FLAG)) st_release_gpu(P.ws.flags + slot_id, 1u);
+        } else {
+          // Count this arrival at the tile's owner o; the contributor that
+          // completes the count (pl - o earlier arrivals) sums the tile.
+          const ProbSched &q = P.ps[w.problem];
+          const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
+          o = unit_of_iter(S, ts);
+          pl = unit_of_iter(S, ts + q.iters - 1);
+          bool mine = false;
+          if (et == 0) mine = atom_add_acq_rel_gpu(P.ws.flags + cslot(o), 1u) == (uint32_t)(pl - o);
+          do_sum = broadcast(mine);
+          own_tmem = false;
+        }
+      } else if (w.role == ROLE_OWNER) {
+        if (!last_arriver) {
+          // Poll every peer's flag with relaxed loads (they overlap), then
+          // one acquire fence orders the partial reads after the peers'
+          // release stores.
           if (et == 0) {
-            // Poll every peer's flag with relaxed loads (they overlap), then
-            // one acquire fence orders the partial reads after the peers'
-            // release stores.
             const uint64_t t0 = globaltimer();
             for (;;) {
               bool all = true;
-              for (int p = w.peer_first; p <= w.peer_last; ++p)
-                all &= ld_relaxed_gpu(P.ws.flags + (PAIR ? 2 * p + (int)rank : p)) != 0u;
+              for (int p = w.peer_first; p <= w.peer_last; ++p) all &= ld_relaxed_gpu(P.ws.flags + cslot(p)) != 0u;
               if (all) break;
               if (globaltimer() - t0 > tmo) {
                 atomicExch(P.ws.status, STATUS_TIMEOUT);
@@ -484,145 +694,50 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           }
           named_bar_sync(1, 128);
-        }
-        float alpha = pr.alpha;
-        if (IN == IN_E4M3) {
-          if (pr.scale_a) alpha *= *pr.scale_a;
-          if (pr.scale_b) alpha *= *pr.scale_b;
-        }
-        const int grow = w.tm * BM + (int)rank * 128 + row;
-        const int row0 = w.tm * BM + (int)rank * 128 + q4 * 32;   // first row of this warp
-        auto store_chunk = [&](int ch, const float (&v)[32]) {
-          if (pr.c_tma) {
-            // Stage the chunk in shared memory and write it with one TMA
-            // store per 128-byte-wide box (BF16: 64 columns = two chunks;
-            // FP32: 32 columns); TMA clips rows/columns outside C.
-            constexpr bool F32OUT = sizeof(OutT) == 4;
-            const int part = F32OUT ? 0 : (ch & 1);
-            uint8_t *buf = my_stage + sbuf * 4096;
-            if (part == 0) {
-              if (lane == 0) bulk_wait_group_read<1>();   // this buffer's previous store has read it
-              __syncwarp();
-            }
-            uint8_t *rowp = buf + lane * 128;
-            if constexpr (F32OUT) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q)
-                *reinterpret_cast<float4 *>(rowp + ((q ^ (lane & 7)) * 16)) =
-                    make_float4(alpha * v[4 * q], alpha * v[4 * q + 1], alpha * v[4 * q + 2], alpha * v[4 * q + 3]);
-            } else {
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                uint4 pk;
-                __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&pk);
-#pragma unroll
-                for (int e = 0; e < 4; ++e)
-                  h[e] = __floats2bfloat162_rn(alpha * v[8 * q + 2 * e], alpha * v[8 * q + 2 * e + 1]);
-                *reinterpret_cast<uint4 *>(rowp + (((part * 4 + q) ^ (lane & 7)) * 16)) = pk;
-              }
-            }
-            if (F32OUT || part == 1) {
-              fence_proxy_async_smem_cta();
-              __syncwarp();
-              if (lane == 0) {
-                tma_store_2d(&P.tmap_c[0], smem_u32(buf), w.tn * BN + (ch - part) * 32, row0);
-                bulk_commit_group();
-              }
-              sbuf ^= 1;
-            }
-          } else if (grow < pr.M) {
-            const int gcol = w.tn * BN + ch * 32;
-            if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
-          }
-        };
-        if (w.role != ROLE_OWNER) {
-#pragma unroll 1
-          for (int ch = 0; ch < BN / 32; ++ch) {
-            float v[32];
-            tmem_ld32(tbase + ch * 32, v);
-            store_chunk(ch, v);
-          }
-        } else if (c.it >= c.end && c.dp >= S.total_tiles) {
-          // This owner item is the CTA's last: every MMA has completed, so
-          // the operand ring in shared memory is free.  Stage the peers'
-          // partials there with bulk copies, 16 KB units (chunk, peer) in
-          // chunk-major order, up to FIX_SMEM_UNITS in flight; then add
-          // them in the fixed order (own accumulator, peers ascending).
-          constexpr int NCH = BN / 32;
-          const int np = w.peer_last - w.peer_first + 1;
-          const int nunits = NCH * np;
-          int nb = (stages * STAGE_BYTES) / FIX_UNIT_BYTES;
-          if (nb > FIX_SMEM_UNITS) nb = FIX_SMEM_UNITS;
-          float v[32];
-          bool ok = true;
-          int group = 0;
-          for (int g0 = 0; g0 < nunits && ok; g0 += nb, ++group) {
-            const int gn = nunits - g0 < nb ? nunits - g0 : nb;
-            if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
-            if (et == 0) {
-              fence_proxy_async_all();   // the acquired partials, to the copy engine
-              for (int b = 0; b < gn; ++b) {
-                const int i = g0 + b;
-                const int ch = i / np;
-                const int p = w.peer_first + (i - ch * np);
-                const float4 *src = slots + (int64_t)(PAIR ? 2 * p + (int)rank : p) * SLOT_F4 + (ch * 8) * 128;
-                const uint32_t fb = smem_u32(fix_bar + b);
-                mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
-                bulk_copy_g2s(tiles_addr + b * FIX_UNIT_BYTES, src, FIX_UNIT_BYTES, fb);
-              }
-            }
-            for (int b = 0; b < gn; ++b) {
-              const int i = g0 + b;
-              const int ch = i / np;
-              const int pi = i - ch * np;
-              if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(fix_bar + b), (uint32_t)(group & 1), tmo))) {
-                fail();
-                ok = false;
-                break;
-              }
-              if (tr_lead && group == 0 && b == 0) trace_put(trace, TRACE_FIX_BASE + 1, 12, nitem, globaltimer_ordered());
-              if (tr_lead && group == 0 && b == gn - 1) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
-              if (pi == 0) tmem_ld32(tbase + ch * 32, v);
-              const float4 *sb = reinterpret_cast<const float4 *>(smem + b * FIX_UNIT_BYTES);
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float4 q = sb[j * 128 + row];
-                v[4 * j] += q.x;
-                v[4 * j + 1] += q.y;
-                v[4 * j + 2] += q.z;
-                v[4 * j + 3] += q.w;
-              }
-              if (pi == np - 1) store_chunk(ch, v);
-            }
-            named_bar_sync(1, 128);   // every thread is done with the group's buffers
-          }
+          do_sum = true;
         } else {
-          // An owner item followed by more work: its fixup overlaps the next
-          // item's MMAs, so a plain loop suffices.  Fixed summation order:
-          // own accumulator, then peers in ascending unit index.
-#pragma unroll 1
-          for (int ch = 0; ch < BN / 32; ++ch) {
-            float v[32];
-            tmem_ld32(tbase + ch * 32, v);
-            for (int p = w.peer_first; p <= w.peer_last; ++p) {
-              const float4 *src = slots + (int64_t)(PAIR ? 2 * p + (int)rank : p) * SLOT_F4 + (ch * 8) * 128 + row;
-#pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float4 q = __ldcg(src + j * 128);
-                v[4 * j] += q.x;
-                v[4 * j + 1] += q.y;
-                v[4 * j + 2] += q.z;
-                v[4 * j + 3] += q.w;
-              }
-            }
-            store_chunk(ch, v);
+          // If every peer has already arrived, sum now from TMEM; otherwise
+          // spill to the owner slot and count this arrival too.
+          const uint32_t npeers = (uint32_t)(w.peer_last - w.peer_first + 1);
+          bool mine = false;
+          if (et == 0) {
+            mine = ld_relaxed_gpu(P.ws.flags + slot_id) == npeers;
+            if (mine) fence_acq_rel_gpu();
+          }
+          do_sum = broadcast(mine);
+          if (!do_sum) {
+            spill(oslots + (int64_t)slot_id * SLOT_F4);
+            __threadfence();
+            named_bar_sync(1, 128);
+            if (et == 0) mine = atom_add_acq_rel_gpu(P.ws.flags + slot_id, 1u) == npeers;
+            do_sum = broadcast(mine);
           }
         }
-        release_acc(acc);
-        if (w.role == ROLE_OWNER && et == 0)
-          for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[PAIR ? 2 * p + (int)rank : p] = 0u;
-        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
+      } else {
+        const float alpha = get_alpha();
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 32; ++ch) {
+          float v[32];
+          tmem_ld32(tbase + ch * 32, v);
+          store_chunk(ch, v, alpha);
+        }
       }
+      if (do_sum) {
+        if (own_tmem)
+          fixup_sum(std::true_type{}, o, pl);
+        else
+          fixup_sum(std::false_type{}, o, pl);
+        // Self-cleaning: the owner protocol clears the peers' flags, the
+        // last-arriver protocol the tile's counter.
+        if (et == 0) {
+          if (!last_arriver)
+            for (int p = w.peer_first; p <= w.peer_last; ++p) P.ws.flags[cslot(p)] = 0u;
+          else
+            P.ws.flags[cslot(o)] = 0u;
+        }
+      }
+      if (w.role != ROLE_PEER) release_acc(acc);
+      if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       ++nitem;
       if (++acc == 2) {
         acc = 0;

@@ -192,6 +192,7 @@ struct Cfg {
   int debug_flags;
   uint64_t *trace;
   int raster_group;
+  int fixup;       // FIXUP_OWNER or FIXUP_LAST_ARRIVER
   int ctas() const { return pair ? 2 * g : g; }
 };
 
@@ -235,14 +236,18 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.trace = d.trace;
   if (d.raster_group < 0 || d.raster_group > 64) return SK_ERR_INVALID_ARG;
   r.raster_group = d.raster_group ? d.raster_group : GROUP_M_DEFAULT;
+  if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER) return SK_ERR_INVALID_ARG;
+  r.fixup = d.fixup == SK_FIXUP_LAST_ARRIVER ? FIXUP_LAST_ARRIVER : FIXUP_OWNER;
   *out = r;
   return SK_OK;
 }
 
-// One partial slot (128 rows x BN FP32) and one flag per CTA.
+// Per CTA one partial slot (128 rows x BN FP32) and one flag; the
+// last-arriver fixup adds a second slot per CTA for its owner segment.
 size_t ws_bytes_for(const Cfg &c) {
   const size_t flags = ((size_t)c.ctas() * 4 + 255) / 256 * 256;
-  return 256 + flags + (size_t)c.ctas() * 128 * c.BN * 4;
+  const size_t slots = (size_t)c.ctas() * 128 * c.BN * 4;
+  return 256 + flags + (c.fixup == FIXUP_LAST_ARRIVER ? 2 : 1) * slots;
 }
 
 Workspace carve(void *ws, const Cfg &c) {
@@ -252,6 +257,7 @@ Workspace carve(void *ws, const Cfg &c) {
   w.flags = reinterpret_cast<uint32_t *>(b + 256);
   const size_t flags = ((size_t)c.ctas() * 4 + 255) / 256 * 256;
   w.partials = reinterpret_cast<float *>(b + 256 + flags);
+  w.owner_partials = c.fixup == FIXUP_LAST_ARRIVER ? w.partials + (size_t)c.ctas() * 128 * c.BN : nullptr;
   return w;
 }
 
@@ -583,6 +589,7 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   P->stages = c.stages;
   P->debug_flags = c.debug_flags;
   P->trace = c.trace;
+  P->fixup = c.fixup;
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
   if (c.fam == FAM_BF16) {
@@ -658,6 +665,7 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
   P->ws = ws;
   P->timeout_ns = c.timeout_ns;
   P->debug_flags = c.debug_flags;
+  P->fixup = c.fixup;
   cudaError_t e = launch_simt_f32<MAXP>(*P, pl.grid, st);
   delete P;
   return cuda_err(e, "FP32 GEMM launch");

@@ -105,6 +105,28 @@ def test_workspace_size(sk):
         q = sk.shape_problem(*shape)
         assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
         assert n.value <= 256 + 768 + 148 * 128 * 256 * 4
+    # the last-arriver fixup keeps a second slot per CTA (owner segments)
+    for tile in ((128, 128), (128, 256), (256, 256)):
+        c = sk.api._cfg({"num_ctas": 148, "tile_m": tile[0], "tile_n": tile[1], "fixup": "last_arriver"})
+        assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+        assert n.value == 256 + 768 + 2 * 148 * 128 * tile[1] * 4
+    c = sk.api._cfg({"num_ctas": 148, "fixup": 2})
+    assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_INVALID_ARG
+
+
+def test_default_workspace_fits_both_fixups(sk):
+    """The default workspace holds the largest plan of either fixup."""
+    B = sk.binding
+    n = ctypes.c_size_t(0)
+    sms = 148
+    default = 256 + (-(-sms * 4 // 256)) * 256 + 2 * sms * 128 * 256 * 4
+    assert sk.api.default_workspace_bytes(sms) == default
+    for fix in ("owner", "last_arriver"):
+        for shape in [(384, 384, 2048), (8192, 8192, 8192), (128, 8192, 16384), (1536, 1536, 8192)]:
+            c = sk.api._cfg({"num_ctas": sms, "fixup": fix})
+            q = sk.shape_problem(*shape)
+            assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+            assert n.value <= default
 
 
 def test_gemm_without_device_reports_no_device(sk):

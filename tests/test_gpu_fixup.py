@@ -1,0 +1,136 @@
+"""The last-arriver fixup against the owner-waits fixup and the FP64 oracle.
+
+Both protocols add the partials of a split tile in the same order (the
+partial holding k-block 0, then the other units' partials by ascending unit
+index), so their outputs must agree bit for bit whatever the arrival order
+was; the oracle bound holds for both.  Counters must be back at zero after
+every call, so calls with either protocol can share one workspace.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import fp8
+import workloads
+from gpu_common import assert_within_bound, dev, same_strides, sk, to_np
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(128, 128), (128, 256), (256, 256)]
+
+
+@pytest.fixture(scope="module")
+def m():
+    return sk()
+
+
+def _both(m, call, **cfg):
+    ws = m.default_workspace(dev())
+    c0 = call(m.Config(fixup="owner", **cfg))
+    c1 = call(m.Config(fixup="last_arriver", **cfg))
+    assert ws.status() == 0
+    return c0, c1
+
+
+def _flags_zero(m):
+    """Every flag / counter word of the default workspace is zero."""
+    ws = m.default_workspace(dev())
+    sms = torch.cuda.get_device_properties(ws.device).multi_processor_count
+    words = ws.buf[256:256 + 4 * sms].view(torch.int32)
+    return int(words.abs().sum().item()) == 0
+
+
+@pytest.mark.parametrize("tile", TILES)
+@pytest.mark.parametrize("mode", ["sk", "hybrid1", "hybrid2"])
+@pytest.mark.parametrize("num_ctas", [0, 6, 34])
+def test_bf16_last_arriver_bitwise(m, tile, mode, num_ctas):
+    # ragged M and N, K not a multiple of the 64-wide k-block
+    a, b = workloads.gemm_inputs(392, 776, 1544, dtype="bf16", seed=61)
+    d = dev()
+    A, Bm = same_strides(a, d), same_strides(b, d)
+    c0, c1 = _both(m, lambda cfg: m.gemm(A, Bm, out_dtype=torch.float32, config=cfg),
+                   tile_m=tile[0], tile_n=tile[1], mode=mode, num_ctas=num_ctas)
+    assert torch.equal(c0, c1), (tile, mode, num_ctas)
+    assert _flags_zero(m)
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_bf16_last_arriver_oracle(m, tile):
+    """BF16 output, many units per tile (K = 8192 over 36 or 72 tiles)."""
+    a, b = workloads.gemm_inputs(1536, 1536, 8192, dtype="bf16", seed=62)
+    d = dev()
+    c = m.gemm(same_strides(a, d), same_strides(b, d),
+               config=m.Config(fixup="last_arriver", mode="sk", tile_m=tile[0], tile_n=tile[1]))
+    assert m.default_workspace(d).status() == 0
+    r = torch.arange(0, 1536, 97)
+    assert_within_bound(c[r.to(d)], a[r], b, out="bf16", what=f"last-arriver {tile}")
+    assert _flags_zero(m)
+
+
+def test_bf16_last_arriver_int_exact_repeat(m):
+    """Integer inputs (every partial sum exact): equal to the oracle, and
+    identical over repeated calls sharing the workspace with owner calls."""
+    a, b = workloads.gemm_inputs(520, 1032, 4104, dtype="bf16", seed=63, dist="int")
+    d = dev()
+    A, Bm = same_strides(a, d), same_strides(b, d)
+    ref, _ = oracle.gemm(a, b)
+    for i in range(3):
+        for fix in ("last_arriver", "owner"):
+            c = m.gemm(A, Bm, out_dtype=torch.float32, config=m.Config(fixup=fix, mode="sk", num_ctas=76))
+            assert np.array_equal(to_np(c), ref), (i, fix)
+    assert m.default_workspace(d).status() == 0
+    assert _flags_zero(m)
+
+
+@pytest.mark.parametrize("num_ctas", [0, 5, 40])
+def test_f32_last_arriver_bitwise(m, num_ctas):
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=64)
+    d = dev()
+    A, Bm = same_strides(a, d), same_strides(b, d)
+    c0, c1 = _both(m, lambda cfg: m.gemm(A, Bm, config=cfg), mode="sk", num_ctas=num_ctas)
+    assert torch.equal(c0, c1)
+    assert_within_bound(c1, a, b, out="f32", what="f32 last-arriver")
+    assert _flags_zero(m)
+
+
+@pytest.mark.parametrize("tile_m", [128, 256])
+def test_fp8_last_arriver_bitwise(m, tile_m):
+    d = dev()
+    xa = workloads.normal((300, 1024), seed=65)
+    xb = workloads.normal((520, 1024), seed=66)
+    qa, sa = m.quantize_e4m3(xa.to(d).contiguous())
+    qb, sb = m.quantize_e4m3(xb.to(d).contiguous())
+    A = qa.view(torch.float8_e4m3fn)
+    Bm = qb.view(torch.float8_e4m3fn).t()
+    c0, c1 = _both(m, lambda cfg: m.gemm(A, Bm, out_dtype=torch.float32, scale_a=sa, scale_b=sb, config=cfg),
+                   mode="sk", tile_m=tile_m)
+    assert torch.equal(c0, c1)
+    deq_a = fp8.dequantize_e4m3(qa.cpu().numpy(), sa.item())
+    deq_b = fp8.dequantize_e4m3(qb.cpu().numpy(), sb.item()).T
+    assert_within_bound(c1, deq_a, deq_b, out="f32", what="fp8 last-arriver")
+
+
+@pytest.mark.parametrize("tile_m", [128, 256])
+def test_grouped_last_arriver_bitwise(m, tile_m):
+    d = dev()
+    shapes = [(256, 1024, 1024), (300, 512, 2048), (1024, 768, 128), (512, 2048, 64), (777, 256, 4096)]
+    As, Bs = [], []
+    for i, (M, N, K) in enumerate(shapes):
+        a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=90 + i)
+        As.append(a.to(d))
+        Bs.append(b.to(d))
+    o0, o1 = _both(m, lambda cfg: m.grouped_gemm(As, Bs, out_dtype=torch.float32, config=cfg),
+                   mode="sk", tile_m=tile_m)
+    for x, y, s in zip(o0, o1, shapes):
+        assert torch.equal(x, y), s
+    assert _flags_zero(m)
+
+
+def test_backward_last_arriver_bitwise(m):
+    a, b = workloads.gemm_inputs(264, 392, 520, dtype="bf16", seed=67)
+    d = dev()
+    dC = workloads.draw((264, 392), 69, "uniform").to(torch.bfloat16).to(d)
+    A, Bm = same_strides(a, d), same_strides(b, d)
+    r0, r1 = _both(m, lambda cfg: m.gemm_backward(A, Bm, dC, config=cfg), mode="sk")
+    assert torch.equal(r0[0], r1[0]) and torch.equal(r0[1], r1[1])
