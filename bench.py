@@ -266,6 +266,31 @@ def run_ours(args, world, rank, local):
         })
     dp_step_ms = sum(statistics.mean(v) for v in dp_ms)
 
+    # ---- best fixed-tile configurations: every candidate (tile x stages x
+    # mode) timed on this GPU; the best DP one is the data-parallel baseline
+    # a hand-tuned fixed-tile kernel would reach, the best SK one bounds what
+    # the library's own choice leaves on the table.
+    best_dp_ms, best_sk_ms = [], []
+    if args.search:
+        for entry, (a, b, c) in zip(per_shape, data):
+            res = []
+            for cfg, _pred in sk.autotune.candidates(sk.make_problem(a, b, c)):
+                for _ in range(2):
+                    sk.gemm(a, b, c, config=cfg, workspace=ws)
+                ms = _timed_region(lambda: sk.gemm(a, b, c, config=cfg, workspace=ws), args.search_steps,
+                                   lambda: l2_flush(0))
+                res.append((cfg, ms))
+            f = workloads.gemm_flops(entry["M"], entry["N"], entry["K"])
+            for key, sel, acc in (("best_dp", lambda m: m == "dp", best_dp_ms),
+                                  ("best_sk", lambda m: m != "dp", best_sk_ms)):
+                cfg, ms = min((r for r in res if sel(r[0].mode)), key=lambda r: r[1])
+                acc.append(ms)
+                entry[key] = {"tile": f"{cfg.tile_m}x{cfg.tile_n}", "stages": cfg.stages, "mode": cfg.mode,
+                              "ms": round(ms, 4), "tflops": round(f / ms / 1e9, 1)}
+            entry["candidates_timed"] = len(res)
+        if ws.status() != 0:
+            raise RuntimeError("device status after the candidate search")
+
     # roofline of the dominant launch (the 8192^3 GEMM)
     di = shapes.index(DOMINANT_SHAPE) if DOMINANT_SHAPE in shapes else 0
     dom_ms = statistics.mean(sk_ms[di])
@@ -292,6 +317,10 @@ def run_ours(args, world, rank, local):
         "dp_baseline": {"value": round(sum(flops) / (dp_step_ms / 1e3) / 1e12, 2), "unit": UNIT,
                         "ms_per_step": round(dp_step_ms, 4)},
         "shapes": per_shape,
+        "best_fixed_tile": None if not best_dp_ms else {
+            "dp": {"value": round(sum(flops) / (sum(best_dp_ms) / 1e3) / 1e12, 2), "unit": UNIT},
+            "sk": {"value": round(sum(flops) / (sum(best_sk_ms) / 1e3) / 1e12, 2), "unit": UNIT},
+            "protocol": f"every tile x stages x mode candidate, median of {args.search_steps} runs, L2 flushed"},
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": len(shapes) * args.steps,
@@ -361,7 +390,7 @@ def _timed_region(fn, steps, flush):
 
 
 def run_workload(args, world, rank, local):
-    """FP8, grouped and autograd configurations, measured like the sweep
+    """FP8, grouped, autograd and FP32 configurations, measured like the sweep
     (inputs resident, L2 flushed, CUDA events), each next to its
     data-parallel counterpart."""
     import paper_2407_00044_gb300 as sk
@@ -458,6 +487,24 @@ def run_workload(args, world, rank, local):
         tdp = _timed_region(lambda: step(dp), steps, flush)
         rows.append((f"{M}x{N}x{K} fwd+bwd", f, t, tdp))
         desc = "autograd BF16 layer: forward C=A*B plus backward dA=dC*B^T, dB=A^T*dC"
+    elif args.workload == "f32":
+        # FFMA peak derived from the unit counts: SMs x 128 FP32 lanes x 2 flop
+        # x the maximum SM clock (2070 MHz on GB300); nothing measured.
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * 128 * 2 * 2.07e9 / 1e12
+        peak_note = f"FFMA ALU peak {sms} SMs x 128 lanes x 2 flop x 2.07 GHz (derived)"
+        M, N, K = (workloads.FP32_SMALL[x] for x in ("M", "N", "K"))
+        A = workloads.device_uniform((M, K), seed=5000, device=dev, dtype=torch.float32)
+        Bm = workloads.device_uniform((N, K), seed=5001, device=dev, dtype=torch.float32).t()
+        C = torch.empty(M, N, dtype=torch.float32, device=dev)
+        for cfg in (auto, dp):
+            for _ in range(args.warmup):
+                sk.gemm(A, Bm, C, config=cfg)
+        t = _timed_region(lambda: sk.gemm(A, Bm, C, config=auto), steps, flush)
+        tdp = _timed_region(lambda: sk.gemm(A, Bm, C, config=dp), steps, flush)
+        rows.append((f"{M}x{N}x{K} f32", workloads.gemm_flops(M, N, K), t, tdp))
+        desc = (f"FP32 {M}x{N}x{K}, A row-major, B column-major, uniform[-1,1]; 128x128 tiles "
+                "(9 tiles, fewer than SMs: every tile is split), FFMA SIMT kernel")
     else:
         raise ValueError(args.workload)
     if ws_status(sk, dev) != 0:
@@ -471,10 +518,11 @@ def run_workload(args, world, rank, local):
     return {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": args.warmup, "ms_per_step": round(tot_t, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "e4m3" if args.workload == "fp8" else "bf16", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp8": "e4m3", "f32": "f32"}.get(args.workload, "bf16"), "data": "synthetic",
         "config": {"workload": desc, "l2": "flushed (write then read 256 MB) before every timed run"},
         "dp_baseline": {"value": round(tot_f / (tot_dp / 1e3) / 1e12, 2), "unit": UNIT},
-        "rows": [{"case": r[0], "ms": round(r[2], 4), "tflops": round(r[1] / r[2] / 1e9, 1),
+        "rows": [{"case": r[0], "ms": round(r[2], 4), "us": round(1e3 * r[2], 2), "dp_us": round(1e3 * r[3], 2),
+                  "tflops": round(r[1] / r[2] / 1e9, 2),
                   "pct_peak": round(100 * r[1] / r[2] / 1e9 / peak, 1), "dp_ms": round(r[3], 4),
                   "dp_tflops": round(r[1] / r[3] / 1e9, 1)} for r in rows],
         "peak": {"value": peak, "source": peak_note},
@@ -571,7 +619,10 @@ def main(argv=None):
     ap.add_argument("--mode", default="auto", choices=["auto", "dp", "sk", "hybrid1", "hybrid2"])
     ap.add_argument("--no-dp", dest="dp", action="store_false", help="skip the data-parallel baseline")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer run")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "fp8", "grouped", "autograd"],
+    ap.add_argument("--no-search", dest="search", action="store_false",
+                    help="skip timing every fixed tile/stages/mode candidate of the sweep shapes")
+    ap.add_argument("--search-steps", type=int, default=20)
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "fp8", "grouped", "autograd", "f32"],
                     help="sweep (default, the headline) or one of the other configurations")
     args = ap.parse_args(argv)
     if args.warmup < 3 and args.impl == "ours":

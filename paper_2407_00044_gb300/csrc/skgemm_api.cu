@@ -340,40 +340,47 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // Analytic makespan of a plan, used to choose the tile and the DP/SK split
 // when the caller leaves them to the library (the paper's Results and
 // Future Work name such a predictive load-balancing model, "Block2Time").
-// Each unit's time is the sum over its work items of
-//   k-blocks x t_iter + t_item (+ fixup cost if the item is an owner, which
-//   lies on the critical path only when it is the CTA's last item, when
-//   every peer finishes at the same time and must spill first),
-// the kernel's time is the slowest unit plus a launch cost, and never less
-// than the DRAM bytes its operand loads cost at HBM bandwidth (see
-// plan_dram_bytes: Stream-K ranges lose the L2 sharing of DP waves).  The per-k-block times
-// are measured figures of these kernels on GB300 (8192^3: 0.345 us per
-// 256x256x64 pair step with 6 stages, 0.40 us per 128x256x64 CTA step; a
-// 128x128x64 step also costs ~0.40 us: it is bound by shared-memory
-// bandwidth, not the tensor pipe).
+//
+// Each unit is simulated as the kernel runs it: an MMA chain (k-blocks x
+// t_iter + t_mac_item per item) feeding an epilogue chain through two TMEM
+// accumulators, so item i's MMAs wait for the epilogue of item i-2.  The
+// epilogue of an item costs
+//   whole / DP tile : t_store
+//   peer            : t_spill                      (and records when the
+//                                                   partial is visible)
+//   owner           : t_fix_base + peers x t_fix_peer + t_store, after every
+//                     peer's partial is visible; t_fix_peer is the staged
+//                     (last item) or the plain (more work follows) rate.
+// The FP32 SIMT kernel has no separate epilogue warps: its chains are one.
+// When the plan's DRAM bytes at HBM bandwidth exceed the longest MMA chain
+// (see plan_dram_bytes: Stream-K ranges lose the L2 sharing of DP waves),
+// every MMA chain is stretched by that ratio; the fixup tail still follows.
+// The kernel's time is the latest unit end plus a launch cost.
+// Coefficients: least-squares fit (log time) to every default-stage
+// candidate of 23 BF16 shapes timed on GB300 (cross-validated on
+// half-splits: the choice costs 0.6 % on average against the measured best).
+constexpr double PAIR_ITER_NS = 270.0, PAIR_MAC_ITEM_NS = 3520.0, PAIR_LAUNCH_NS = 3040.0, PAIR_STORE_NS = 4150.0,
+                 PAIR_SPILL_NS = 11430.0, PAIR_FIX_BASE_NS = 0.0, PAIR_FIX_PEER_LAST_NS = 1270.0,
+                 PAIR_FIX_PEER_MID_NS = 3690.0;
+
 struct ModelCoeffs {
-  double iter_ns;         // one k-block of one tile
-  double item_ns;         // per work item (tile switch, epilogue not hidden)
-  double launch_ns;       // launch, prologue, pipeline fill and the last epilogue
-  double owner_last_ns;   // owner fixup as the CTA's last item: peers' spill + first partial
-  double owner_mid_ns;    // owner fixup followed by more work (mostly hidden)
-  double peer_extra_ns;   // each further peer partial of a last-item fixup
-  double spill_last_ns;   // peer spill as the CTA's last item
+  double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
+  double mac_item_ns;        // per work item on the MMA chain (tile switch, pipeline refill)
+  double launch_ns;          // launch and prologue
+  double store_ns;           // epilogue of a finished tile (TMEM -> C)
+  double spill_ns;           // a peer's partial to the workspace
+  double fix_base_ns;        // owner fixup, fixed part
+  double fix_peer_last_ns;   // per peer partial, staged fixup (the CTA's last item)
+  double fix_peer_mid_ns;    // per peer partial, plain fixup (more work follows)
+  bool serial;               // epilogue on the same threads as the MMA chain
 };
 
-// Figures measured on GB300 (per-CTA timeline traces and config sweeps).
 ModelCoeffs model_coeffs(const Cfg &c) {
-  ModelCoeffs m;
-  if (c.fam == FAM_F32) {
-    m = {1700.0, 500.0, 6000.0, 4000.0, 800.0, 1000.0, 2000.0};
-  } else if (c.pair) {
-    m = {c.stages >= 6 ? 345.0 : 370.0, 400.0, 11500.0, 8000.0, 1000.0, 2500.0, 3000.0};
-  } else if (c.BN == 256) {
-    m = {400.0, 300.0, 10000.0, 7000.0, 1000.0, 2000.0, 3000.0};
-  } else {
-    m = {400.0, 250.0, 10000.0, 5000.0, 800.0, 1500.0, 2000.0};
-  }
-  return m;
+  if (c.fam == FAM_F32) return {1700.0, 500.0, 6000.0, 1000.0, 2000.0, 1000.0, 1000.0, 1000.0, true};
+  if (c.pair) return {PAIR_ITER_NS, PAIR_MAC_ITEM_NS, PAIR_LAUNCH_NS, PAIR_STORE_NS, PAIR_SPILL_NS, PAIR_FIX_BASE_NS,
+                      PAIR_FIX_PEER_LAST_NS, PAIR_FIX_PEER_MID_NS, false};
+  if (c.BN == 256) return {320.0, 4250.0, 0.0, 4890.0, 9350.0, 360.0, 1360.0, 3170.0, false};
+  return {250.0, 3310.0, 1630.0, 3810.0, 570.0, 1300.0, 630.0, 910.0, false};
 }
 
 double algorithmic_dram_bytes(const std::vector<Norm> &work) {
@@ -459,23 +466,59 @@ double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const C
 
 double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
   const ModelCoeffs k = model_coeffs(c);
-  double crit = 0;
+  const Sched &s = pl.s;
+  if (s.num_problems <= 0) return k.launch_ns;
+  std::vector<std::vector<Item>> items((size_t)c.g);
+  double longest_mac = 0;
   for (int u = 0; u < c.g; ++u) {
     Cursor cur;
-    cursor_init(pl.s, u, cur);
+    cursor_init(s, u, cur);
     Item w;
-    double t = 0;
-    while (pl.s.num_problems > 0 && cursor_next(pl.s, pl.ps.data(), u, cur, w)) {
-      const bool last = cur.it >= cur.end && cur.dp >= pl.s.total_tiles;
-      t += (w.k1 - w.k0) * k.iter_ns + k.item_ns;
-      if (w.role == ROLE_OWNER)
-        t += last ? k.owner_last_ns + (w.peer_last - w.peer_first) * k.peer_extra_ns : k.owner_mid_ns;
-      if (w.role == ROLE_PEER && last) t += k.spill_last_ns;
+    double mac = 0;
+    while (cursor_next(s, pl.ps.data(), u, cur, w)) {
+      items[u].push_back(w);
+      mac += (w.k1 - w.k0) * k.iter_ns + k.mac_item_ns;
     }
-    crit = std::max(crit, t);
+    longest_mac = std::max(longest_mac, mac);
   }
-  const double dram = std::max(algorithmic_dram_bytes(work), plan_dram_bytes(work, pl, c));
-  return k.launch_ns + std::max(crit, dram / kHbmBytesPerNs);
+  const double dram_ns = std::max(algorithmic_dram_bytes(work), plan_dram_bytes(work, pl, c)) / kHbmBytesPerNs;
+  const double stretch = longest_mac > 0 ? std::max(1.0, dram_ns / longest_mac) : 1.0;
+  // Two passes: the first finds when each peer's partial is visible (a
+  // peer segment is a unit's first item, so it depends on no owner), the
+  // second lets owners wait for them.
+  std::vector<double> spill_done((size_t)c.g, 0.0);
+  double end = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    end = 0;
+    for (int u = 0; u < c.g; ++u) {
+      const std::vector<Item> &its = items[u];
+      double mac_prev = 0, epi_prev = 0, epi_prev2 = 0;
+      for (size_t i = 0; i < its.size(); ++i) {
+        const Item &w = its[i];
+        const bool last = i + 1 == its.size();
+        const double mac_start = k.serial ? epi_prev : std::max(mac_prev, epi_prev2);
+        const double mac_end = mac_start + (w.k1 - w.k0) * k.iter_ns * stretch + k.mac_item_ns;
+        double start = std::max(mac_end, epi_prev);
+        double e;
+        if (w.role == ROLE_PEER) {
+          e = k.spill_ns;
+          spill_done[u] = start + e;
+        } else if (w.role == ROLE_OWNER) {
+          if (pass > 0)
+            for (int p = w.peer_first; p <= w.peer_last; ++p) start = std::max(start, spill_done[p]);
+          e = k.fix_base_ns + (w.peer_last - w.peer_first + 1) * (last ? k.fix_peer_last_ns : k.fix_peer_mid_ns) +
+              k.store_ns;
+        } else {
+          e = k.store_ns;
+        }
+        mac_prev = mac_end;
+        epi_prev2 = epi_prev;
+        epi_prev = start + e;
+      }
+      end = std::max(end, epi_prev);
+    }
+  }
+  return k.launch_ns + end;
 }
 
 // --------------------------------------------------------------- launches
