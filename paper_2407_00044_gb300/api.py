@@ -58,14 +58,23 @@ def _cfg(config) -> B.sk_config:
     return config.to_c()
 
 
-def layout_of(t: torch.Tensor):
-    """(sk_layout, leading dimension) of a 2-D tensor, from its strides."""
+def layout_of(t: torch.Tensor, prefer=None):
+    """(sk_layout, leading dimension) of a 2-D tensor, from its strides.
+
+    A single row or column is contiguous in both layouts; ``prefer`` picks
+    the one the caller wants then (A row-major and B column-major keep
+    both operands K-major, which the TMA path needs for a vector operand)."""
     if t.dim() != 2:
         raise ValueError("expected a 2-D tensor")
     r, c = t.shape
     if t.numel() == 0:
         return B.SK_ROW_MAJOR, max(1, c)
     s0, s1 = t.stride()
+    pad16 = lambda x: -(-max(1, x) // 16) * 16   # noqa: E731
+    if prefer == B.SK_COL_MAJOR and c == 1 and (s0 == 1 or r == 1):
+        return B.SK_COL_MAJOR, pad16(r)
+    if prefer == B.SK_ROW_MAJOR and r == 1 and (s1 == 1 or c == 1):
+        return B.SK_ROW_MAJOR, pad16(c)
     if s1 == 1 and (r <= 1 or s0 >= max(1, c)):
         ld = s0 if r > 1 else -(-max(1, c) // 16) * 16
         return B.SK_ROW_MAJOR, ld
@@ -90,9 +99,9 @@ def make_problem(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor, *, C_in=Non
     p.a_type = _DTYPES[A.dtype]
     p.b_type = _DTYPES[Bm.dtype]
     p.c_type = _DTYPES[C.dtype]
-    p.a_layout, p.lda = layout_of(A)
-    p.b_layout, p.ldb = layout_of(Bm)
-    p.c_layout, p.ldc = layout_of(C)
+    p.a_layout, p.lda = layout_of(A, B.SK_ROW_MAJOR)
+    p.b_layout, p.ldb = layout_of(Bm, B.SK_COL_MAJOR)
+    p.c_layout, p.ldc = layout_of(C, B.SK_ROW_MAJOR)
     p.A = A.data_ptr()
     p.B = Bm.data_ptr()
     p.C = C.data_ptr()
@@ -200,19 +209,19 @@ def gemm_backward(A: torch.Tensor, Bm: torch.Tensor, dC: torch.Tensor, *, need_d
     N = Bm.shape[1]
     dA = torch.empty_strided(A.shape, A.stride(), dtype=A.dtype, device=A.device) if need_dA else None
     dB = torch.empty_strided(Bm.shape, Bm.stride(), dtype=Bm.dtype, device=Bm.device) if need_dB else None
-    c_layout, lddc = layout_of(dC)
+    c_layout, lddc = layout_of(dC, B.SK_ROW_MAJOR)
     if c_layout != B.SK_ROW_MAJOR:
         raise ValueError("dC must be row-major")
     fwd = B.sk_problem()
     fwd.m, fwd.n, fwd.k = M, N, K
     fwd.a_type, fwd.b_type, fwd.c_type = _DTYPES[A.dtype], _DTYPES[Bm.dtype], _DTYPES[dC.dtype]
-    fwd.a_layout, fwd.lda = layout_of(A)
-    fwd.b_layout, fwd.ldb = layout_of(Bm)
+    fwd.a_layout, fwd.lda = layout_of(A, B.SK_ROW_MAJOR)
+    fwd.b_layout, fwd.ldb = layout_of(Bm, B.SK_COL_MAJOR)
     fwd.c_layout, fwd.ldc = B.SK_ROW_MAJOR, lddc
     fwd.A, fwd.B = A.data_ptr(), Bm.data_ptr()
     fwd.alpha, fwd.beta = 1.0, 0.0
-    ldda = layout_of(dA)[1] if dA is not None else 0
-    lddb = layout_of(dB)[1] if dB is not None else 0
+    ldda = layout_of(dA, B.SK_ROW_MAJOR)[1] if dA is not None else 0
+    lddb = layout_of(dB, B.SK_COL_MAJOR)[1] if dB is not None else 0
     ws = workspace or default_workspace(A.device)
     cfg = _cfg(config)
     B.check(B.sk_gemm_backward(ctypes.byref(fwd), _ptr(dC), lddc, _ptr(dA), ldda, _ptr(dB), lddb,

@@ -259,3 +259,25 @@ def test_raster_group_is_a_bijection(sk, group):
         assert seen == {(i, j) for i in range(tm) for j in range(tn)}
     bad = sk.shape_problem(64, 64, 64)
     assert _q(sk, bad, {"raster_group": 65})[0] == B.SK_ERR_INVALID_ARG
+
+
+def test_layout_of_vector_operands(sk):
+    """A single row or column is contiguous in both layouts; the preferred
+    (K-major) one is returned, with a 16-element-padded leading dimension."""
+    import torch
+    B = sk.binding
+    col = torch.empty(8, 1)
+    assert sk.api.layout_of(col, B.SK_COL_MAJOR) == (B.SK_COL_MAJOR, 16)
+    assert sk.api.layout_of(col.t().contiguous().t(), B.SK_COL_MAJOR) == (B.SK_COL_MAJOR, 16)
+    row = torch.empty(1, 40)
+    assert sk.api.layout_of(row, B.SK_ROW_MAJOR) == (B.SK_ROW_MAJOR, 48)
+    # not vectors: the strides decide
+    assert sk.api.layout_of(torch.empty(8, 24), B.SK_COL_MAJOR) == (B.SK_ROW_MAJOR, 24)
+    assert sk.api.layout_of(torch.empty(24, 8).t(), B.SK_ROW_MAJOR) == (B.SK_COL_MAJOR, 8)
+    # a K x 1 B plans on the tensor-core path (it used to read as row-major, ld 1)
+    a = torch.empty(257, 64, dtype=torch.bfloat16)
+    b = torch.empty(64, 1, dtype=torch.bfloat16)
+    c = torch.empty(257, 1, dtype=torch.float32)
+    p = sk.make_problem(a, b, c)
+    assert (p.b_layout, p.ldb) == (B.SK_COL_MAJOR, 64)
+    assert sk.plan(p, sk.Config(tile_m=128, tile_n=128), num_sms=152).tiles == 3
