@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -570,10 +571,48 @@ def cpu_baseline(seconds: float = 12.0):
         t_total += time.perf_counter() - t0
         done_flops += workloads.gemm_flops(R, N, K)
         rows_used.append(R)
-    return {"value": round(done_flops / t_total / 1e12, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
+    rate_all = done_flops / t_total
+    # one thread, on the first problem's first rows (about 2 s)
+    M, N, K = workloads.BF16_SWEEP[0]
+    R1 = max(1, int(rate_all / threads * 2.0 // (2 * N * K)))
+    a64, b64 = operands(R1, N, K, rng_seed)
+    t0 = time.perf_counter()
+    oracle.gemm(a64, b64, threads=1)
+    rate_one = workloads.gemm_flops(R1, N, K) / (time.perf_counter() - t0)
+    # the FP32 problem (384 x 384 x 2048) in full
+    f = workloads.FP32_SMALL
+    a32 = oracle.to_f64(workloads.uniform((f["M"], f["K"]), seed=rng_seed))
+    b32 = oracle.to_f64(workloads.uniform((f["N"], f["K"]), seed=rng_seed + 1)).T
+    t0 = time.perf_counter()
+    oracle.gemm(a32, b32, threads=threads)
+    t_fp32 = time.perf_counter() - t0
+    sweep_flops = sum(workloads.gemm_flops(*x) for x in workloads.BF16_SWEEP)
+    return {"value": round(rate_all / 1e12, 6), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "first R rows (full N, K) of each sweep problem, R = " + ",".join(map(str, rows_used)) +
                       f"; FP64 triple loop with |A||B| scale; {round(t_total, 1)} s",
-            "seconds": round(t_total, 2)}
+            "seconds": round(t_total, 2),
+            "nproc": os.cpu_count(), "cpu_model": cpu_model(),
+            "single_thread": {"value": round(rate_one / 1e12, 6), "unit": UNIT,
+                              "sample": f"first {R1} rows of {M}x{N}x{K}"},
+            "fp32_384x384x2048_full_s": round(t_fp32, 3),
+            "sweep_full_s_extrapolated": round(sweep_flops / rate_all, 1)}
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (x86 'model name', or the Arm part number)."""
+    try:
+        txt = open("/proc/cpuinfo").read()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model name", "Hardware"):
+        for line in txt.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    parts = sorted({line.split(":", 1)[1].strip() for line in txt.splitlines() if line.startswith("CPU part")})
+    impl = sorted({line.split(":", 1)[1].strip() for line in txt.splitlines() if line.startswith("CPU implementer")})
+    if parts:
+        return f"{platform.machine()} implementer {','.join(impl)} part {','.join(parts)}"
+    return platform.machine()
 
 
 def run_reference(args, world, rank):
