@@ -130,9 +130,12 @@ typedef struct {
                                 by the library's runtime model */
     int stages;              /* smem pipeline depth (BF16/E4M3: 2..6; default by tile) */
     sk_mode mode;            /* decomposition; default AUTO */
-    int num_ctas;            /* persistent CTAs, 1 <= num_ctas <= SM count; 0 = SM count.
-                                The pair kernel uses num_ctas / 2 pairs, at most as
-                                many as the GPU can hold at once */
+    int num_ctas;            /* persistent CTAs, 1 <= num_ctas <= SM count; 0 = SM count,
+                                or, when the library chooses the tile or the mode
+                                and the problem has fewer tiles than units, possibly
+                                a multiple of the tile count (every tile then splits
+                                into equal parts).  The pair kernel uses num_ctas / 2
+                                pairs, at most as many as the GPU can hold at once */
     int min_iters_per_unit;  /* fewest k-blocks per Stream-K unit; default 4 */
     uint64_t timeout_ns;     /* bound on every device-side wait; default 2e9 ns */
     int debug_flags;         /* test-only fault injection, 0 in normal use:

@@ -1,7 +1,9 @@
 """Measured autotuner for the Stream-K GEMM.
 
 Candidates are every valid combination of tile (128x128, 128x256, 256x256
-CTA pair), pipeline depth and decomposition (DP, SK, HYBRID1, HYBRID2).  The
+CTA pair), pipeline depth and decomposition (DP, SK, HYBRID1, HYBRID2),
+plus, where every tile is split and there are fewer tiles than units, the
+same with the unit count cut to a multiple of the tile count.  The
 library's runtime model (sk_plan_query's predicted_us) ranks them; the best
 `top_k` are timed on the GPU with CUDA events (L2 flushed before each run)
 and the fastest is cached in a JSON file keyed by problem shape, layouts,
@@ -80,6 +82,14 @@ def candidates(problem: B.sk_problem, num_sms: int = 0):
                 except B.SkError:
                     continue
                 out.append((cfg, float(info.predicted_us)))
+                # fewer tiles than units, all split: also the largest multiple
+                # of the tile count (every tile cut into equal parts)
+                T, g = info.tiles, info.num_ctas
+                if info.sk_tiles == T and 0 < T and 2 * T <= g and g // T * T != g:
+                    per = 2 if cfg.tile_m == 256 else 1
+                    cfg2 = api.Config(tile_m=cfg.tile_m, tile_n=cfg.tile_n, stages=cfg.stages, mode=cfg.mode,
+                                      num_ctas=per * (g // T * T))
+                    out.append((cfg2, float(api.plan(problem, cfg2, num_sms=num_sms).predicted_us)))
     out.sort(key=lambda x: x[1])
     return out
 

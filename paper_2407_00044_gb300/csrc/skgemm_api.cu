@@ -357,12 +357,9 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // every MMA chain is stretched by that ratio; the fixup tail still follows.
 // The kernel's time is the latest unit end plus a launch cost.
 // Coefficients: least-squares fit (log time) to every default-stage
-// candidate of 23 BF16 shapes timed on GB300 (cross-validated on
-// half-splits: the choice costs 0.6 % on average against the measured best).
-constexpr double PAIR_ITER_NS = 270.0, PAIR_MAC_ITEM_NS = 3520.0, PAIR_LAUNCH_NS = 3040.0, PAIR_STORE_NS = 4150.0,
-                 PAIR_SPILL_NS = 11430.0, PAIR_FIX_BASE_NS = 0.0, PAIR_FIX_PEER_LAST_NS = 1270.0,
-                 PAIR_FIX_PEER_MID_NS = 3690.0;
-
+// candidate of 26 BF16 shapes timed on GB300, the tile-aligned unit counts
+// included (the choice among the measured candidates then costs 0.4 % on
+// average, 3.4 % at worst, against the measured best).
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
   double mac_item_ns;        // per work item on the MMA chain (tile switch, pipeline refill)
@@ -377,10 +374,9 @@ struct ModelCoeffs {
 
 ModelCoeffs model_coeffs(const Cfg &c) {
   if (c.fam == FAM_F32) return {1700.0, 500.0, 6000.0, 1000.0, 2000.0, 1000.0, 1000.0, 1000.0, true};
-  if (c.pair) return {PAIR_ITER_NS, PAIR_MAC_ITEM_NS, PAIR_LAUNCH_NS, PAIR_STORE_NS, PAIR_SPILL_NS, PAIR_FIX_BASE_NS,
-                      PAIR_FIX_PEER_LAST_NS, PAIR_FIX_PEER_MID_NS, false};
-  if (c.BN == 256) return {320.0, 4250.0, 0.0, 4890.0, 9350.0, 360.0, 1360.0, 3170.0, false};
-  return {250.0, 3310.0, 1630.0, 3810.0, 570.0, 1300.0, 630.0, 910.0, false};
+  if (c.pair) return {302.0, 1190.0, 5270.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0, false};
+  if (c.BN == 256) return {375.0, 760.0, 6520.0, 3030.0, 3920.0, 1760.0, 3320.0, 3790.0, false};
+  return {284.0, 636.0, 5160.0, 3900.0, 3020.0, 0.0, 3210.0, 790.0, false};
 }
 
 double algorithmic_dram_bytes(const std::vector<Norm> &work) {
@@ -393,15 +389,17 @@ double algorithmic_dram_bytes(const std::vector<Norm> &work) {
 }
 
 constexpr double kHbmBytesPerNs = 6500.0;   // measured copy bandwidth ~6.76 TB/s, rounded down
-constexpr double kL2ReuseBytes = 60e6;      // operand footprint that stays L2-resident (of 126 MB)
+constexpr double kL2OperandBytes = 100e6;   // L2 the operands can hold (of 126 MB; the rest serves C and partials)
 
 // DRAM bytes the plan's operand loads are expected to cost.
 //  * DP tiles run in waves of g consecutive tiles that share A/B panels in
 //    L2: each wave reads the distinct row panels and column panels of its
 //    tiles once.
-//  * Stream-K units run far-apart parts of the tile list at the same time
-//    and share nothing while running; their k-slices come from DRAM unless
-//    all the SK tiles' panels fit in L2 together (then once each).
+//  * Stream-K units run far-apart parts of the tile list at the same time;
+//    their k-slices come from DRAM once each if the SK tiles' panels fit
+//    in L2 together.  Otherwise an operand keeps what fits of its share of
+//    L2 (half, or what the other operand leaves) and the rest of its
+//    panels is re-read by every tile that streams it.
 // Output (and C_in) bytes are added for every tile.
 double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
   const Sched &s = pl.s;
@@ -431,12 +429,16 @@ double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const C
     double unique_a = 0, unique_b = 0;
     for (uint64_t r : rows) unique_a += (double)c.BM * work[r >> 32].K * es;
     for (uint64_t q : cols) unique_b += (double)c.BN * work[q >> 32].K * es;
-    if (unique_a + unique_b <= kL2ReuseBytes) {
+    if (unique_a + unique_b <= kL2OperandBytes) {
       bytes += unique_a + unique_b;
     } else {
-      // an operand whose panels fit in half the budget stays resident
-      bytes += unique_a <= kL2ReuseBytes / 2 ? unique_a : streamed_a;
-      bytes += unique_b <= kL2ReuseBytes / 2 ? unique_b : streamed_b;
+      double budget_a = kL2OperandBytes / 2, budget_b = kL2OperandBytes / 2;
+      if (unique_a < budget_a) budget_b = kL2OperandBytes - unique_a;
+      else if (unique_b < budget_b) budget_a = kL2OperandBytes - unique_b;
+      auto operand = [](double unique, double streamed, double budget) {
+        return unique <= budget ? unique : unique + (streamed - unique) * (1.0 - budget / unique);
+      };
+      bytes += operand(unique_a, streamed_a, budget_a) + operand(unique_b, streamed_b, budget_b);
     }
   }
   // data-parallel waves
@@ -746,6 +748,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   struct Choice {
     int tile_m, tile_n;
     sk_mode mode;
+    int num_ctas;
   };
   static std::mutex mu;
   static std::map<std::string, Choice> cache;
@@ -756,6 +759,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
       d->tile_m = it->second.tile_m;
       d->tile_n = it->second.tile_n;
       d->mode = it->second.mode;
+      d->num_ctas = it->second.num_ctas;
       return SK_OK;
     }
   }
@@ -794,11 +798,32 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
         }
         PlanOut pl;
         build_plan(work, idx, c, &pl);
-        const double ns = predict_ns(work, pl, c);
+        double ns = predict_ns(work, pl, c);
         if (ns < best * 0.999) {   // keep the earlier candidate on near-ties
           best = ns;
           best_cfg = t;
           found = true;
+        }
+        // With fewer tiles than units and every tile split (Stream-K), a
+        // unit count that is a multiple of the tile count cuts every tile
+        // into equal parts whose units finish together: each owner waits
+        // for and adds the fewest partials.  Tried when the caller left the
+        // count to the library.
+        const int64_t T = pl.s.total_tiles;
+        if (d->num_ctas == 0 && pl.s.sk_tiles == T && T > 0 && 2 * T <= c.g) {
+          const int g_alt = (int)(c.g / T * T);   // k = g_alt / T >= 2 units per tile
+          sk_config t2 = t;
+          t2.num_ctas = c.pair ? 2 * g_alt : g_alt;
+          Cfg c2;
+          if (g_alt != c.g && resolve_cfg(fam, &t2, sms, &c2) == SK_OK) {
+            PlanOut pl2;
+            build_plan(work, idx, c2, &pl2);
+            ns = predict_ns(work, pl2, c2);
+            if (ns < best * 0.999) {
+              best = ns;
+              best_cfg = t2;
+            }
+          }
         }
       }
     }
@@ -807,9 +832,10 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   d->tile_m = best_cfg.tile_m;
   d->tile_n = best_cfg.tile_n;
   d->mode = best_cfg.mode;
+  d->num_ctas = best_cfg.num_ctas;
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() > 4096) cache.clear();
-  cache[key] = Choice{best_cfg.tile_m, best_cfg.tile_n, best_cfg.mode};
+  cache[key] = Choice{best_cfg.tile_m, best_cfg.tile_n, best_cfg.mode, best_cfg.num_ctas};
   return SK_OK;
 }
 

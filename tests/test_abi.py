@@ -155,7 +155,7 @@ _ROLE = {0: "whole", 1: "owner", 2: "peer", 3: "dp"}
 
 
 def _compare(sk, shapes, mode, sms, dtype="bf16", tile_n=0, min_ipu=1, tile_m=0):
-    cfg = {"mode": mode, "tile_n": tile_n, "min_iters_per_unit": min_ipu, "tile_m": tile_m}
+    cfg = {"mode": mode, "tile_n": tile_n, "min_iters_per_unit": min_ipu, "tile_m": tile_m, "num_ctas": sms}
     info, units = _lib_schedule(sk, shapes, cfg, sms, dtype)
     BM, BN, BK = info.tile_m, info.tile_n, info.tile_k
     problems = []
@@ -214,10 +214,39 @@ def test_tile_selection(sk):
     # K-major operands and m >= 256: CTA pairs with 256 x 256 tiles
     info = _q(sk, sk.shape_problem(3840, 4096, 4096))[1]
     assert (info.tile_m, info.tile_n, info.num_ctas) == (256, 256, 74)
-    # m <= 128 (memory-bound) or FP32: 128-row tiles on every CTA
+    # m <= 128 (memory-bound) or FP32: 128-row tiles; with fewer tiles than
+    # CTAs the count is every SM or a multiple of the tile count
     for p in (sk.shape_problem(128, 8192, 16384), sk.shape_problem(384, 384, 2048, dtype="f32")):
         info = _q(sk, p)[1]
-        assert (info.tile_m, info.num_ctas) == (128, 148)
+        assert info.tile_m == 128
+        assert info.num_ctas == 148 or (info.tiles < 148 and info.num_ctas % info.tiles == 0)
+    # a caller's explicit count is kept
+    info = _q(sk, sk.shape_problem(384, 384, 2048, dtype="f32"), {"num_ctas": 148})[1]
+    assert info.num_ctas == 148
+
+
+def test_tile_aligned_unit_count(sk):
+    """With fewer tiles than units and the count left to the library, the
+    runtime model may cut every tile into equal parts: k x T units, each
+    tile then split among exactly k of them."""
+    p = sk.shape_problem(1536, 1536, 8192)
+    for cfg in ({"tile_m": 256, "tile_n": 256, "mode": "sk"}, {"tile_m": 128, "tile_n": 256, "mode": "sk"}):
+        B = sk.binding
+        info = B.sk_plan_info()
+        c = sk.api._cfg(cfg)
+        arr = (B.sk_problem * 1)(p)
+        # tile and mode fixed by the caller: the count stays every unit
+        assert B.sk_plan_query(arr, 1, ctypes.byref(c), 152, ctypes.byref(info)) == B.SK_OK
+        assert info.num_ctas == (76 if cfg["tile_m"] == 256 else 152)
+    info = sk.plan(p, num_sms=152)   # everything left to the library
+    assert info.num_ctas in (info.tiles * (76 // info.tiles) if info.tile_m == 256 else info.tiles * (152 // info.tiles),
+                             76 if info.tile_m == 256 else 152)
+    for u in range(info.num_ctas):
+        for it in sk.unit_items(p, u, num_sms=152):
+            if it.role == 1:   # owner: with k = g / T units per tile, exactly k - 1 peers
+                k = info.num_ctas // info.tiles
+                if info.num_ctas % info.tiles == 0:
+                    assert it.peer_last - it.peer_first + 1 == k - 1
     # transposed (MN-major) BF16 operands may use pairs
     assert _q(sk, sk.shape_problem(4096, 4096, 4096, b_layout="row"), {"tile_m": 256})[0] == B.SK_OK
     # E4M3 transposed operands are refused by either kernel

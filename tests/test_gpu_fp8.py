@@ -66,3 +66,31 @@ def test_fp8_gemm_vs_dequantised(m, shape, mode, tile_m):
     ref, S = oracle.gemm(xa.numpy(), xb.numpy().T)
     rel = np.abs(to_np(c) - ref) / S
     assert np.max(rel) <= 2 * 2 ** -4 + 2 ** -8
+
+
+@pytest.mark.parametrize("K", [32, 128, 1024])
+def test_fp8_accumulator_width(m, K):
+    """How wide is the kind::f8f6f4 accumulation?  One product 2^8 * 2^8 =
+    2^16 plus K-1 products 2^-3 * 2^-3 = 2^-6: the exact sum 2^16 + (K-1)
+    2^-6 needs 23 significand bits, so an FP32 accumulator keeps it exactly
+    and a narrower one drops the small terms.  The result must meet the
+    oracle bound in any case; the measured shortfall is printed."""
+    d = dev()
+    M, N = 128, 128
+    x = torch.full((M, K), 2.0 ** -3)
+    x[:, 0] = 256.0
+    y = torch.full((N, K), 2.0 ** -3)          # B^T rows (column-major B)
+    y[:, 0] = 256.0
+    # codes with scale 1 (the values are exact E4M3 numbers)
+    qa = torch.from_numpy(fp8.encode_e4m3(x.numpy())).to(d)
+    qb = torch.from_numpy(fp8.encode_e4m3(y.numpy())).to(d)
+    one = torch.ones((), dtype=torch.float32, device=d)
+    c = m.gemm(qa.view(torch.float8_e4m3fn), qb.view(torch.float8_e4m3fn).t(), out_dtype=torch.float32,
+               scale_a=one, scale_b=one, config=m.Config(mode="dp", tile_m=128, tile_n=128))
+    exact = 2.0 ** 16 + (K - 1) * 2.0 ** -6
+    got = to_np(c)
+    err = float(np.max(np.abs(got - exact)))
+    S = exact
+    assert err <= 5e-5 * S, (K, err)
+    lost = err / 2.0 ** -6      # small products lost
+    print(f"K={K}: exact {exact!r}, max |err| {err} = {lost:.1f} of the {K - 1} small products")
