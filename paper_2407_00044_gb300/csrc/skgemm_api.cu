@@ -215,10 +215,10 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   } else {
     r.BN = d.tile_n ? d.tile_n : 256;
     if (r.BN != 128 && r.BN != 256) return SK_ERR_UNSUPPORTED;
-    if (r.pair && r.BN != 256) return SK_ERR_UNSUPPORTED;
+    if (r.pair && r.BN != 256 && fam != FAM_BF16) return SK_ERR_UNSUPPORTED;   // 256 x 128 pairs: BF16
     r.BK = fam == FAM_BF16 ? 64 : 128;
     const int stage_bytes = 128 * 128 + (r.pair ? r.BN / 2 : r.BN) * 128;   // per CTA
-    const int max_stages = std::min(6, (227 * 1024 - 1024 - 512 - EPI_STAGE_BYTES) / stage_bytes);
+    const int max_stages = std::min(8, (227 * 1024 - 1024 - 512 - EPI_STAGE_BYTES) / stage_bytes);
     r.stages = d.stages ? d.stages : max_stages;
     if (r.stages < 2 || r.stages > max_stages) return SK_ERR_UNSUPPORTED;
   }
@@ -360,6 +360,11 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // candidate of 26 BF16 shapes timed on GB300, the tile-aligned unit counts
 // included (the choice among the measured candidates then costs 0.4 % on
 // average, 3.4 % at worst, against the measured best).
+// 256 x 128 pair tiles (explicit requests only): each CTA needs 24 KB of
+// operands per 256-cycle k-block, beyond what L2 delivers to one SM, so a
+// k-block costs about what a 256 x 256 one does (measured 8192^3: 986 us).
+#define PAIR128_COEFFS 520.0, 1190.0, 5270.0, 4000.0, 3500.0, 0.0, 2600.0, 3000.0
+
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
   double mac_item_ns;        // per work item on the MMA chain (tile switch, pipeline refill)
@@ -374,6 +379,7 @@ struct ModelCoeffs {
 
 ModelCoeffs model_coeffs(const Cfg &c) {
   if (c.fam == FAM_F32) return {1700.0, 500.0, 6000.0, 1000.0, 2000.0, 1000.0, 1000.0, 1000.0, true};
+  if (c.pair && c.BN == 128) return {PAIR128_COEFFS, false};
   if (c.pair) return {302.0, 1190.0, 5270.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0, false};
   if (c.BN == 256) return {375.0, 760.0, 6520.0, 3030.0, 3920.0, 1760.0, 3320.0, 3790.0, false};
   return {284.0, 636.0, 5160.0, 3900.0, 3020.0, 0.0, 3210.0, 790.0, false};
@@ -638,9 +644,12 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
   if (c.fam == FAM_BF16) {
-    if (c.pair)
+    if (c.pair && c.BN == 256)
       e = f32out ? launch_tc<IN_BF16, float, 256, MAXP, true>(*P, pl.grid, st)
                  : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP, true>(*P, pl.grid, st);
+    else if (c.pair)
+      e = f32out ? launch_tc<IN_BF16, float, 128, MAXP, true>(*P, pl.grid, st)
+                 : launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP, true>(*P, pl.grid, st);
     else if (c.BN == 256)
       e = f32out ? launch_tc<IN_BF16, float, 256, MAXP, false>(*P, pl.grid, st)
                  : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP, false>(*P, pl.grid, st);
@@ -782,7 +791,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
     tns.clear();
     if (fam == FAM_F32) tns.push_back(d->tile_n);
     else if (!free_tile_n) tns.push_back(d->tile_n);
-    else if (tm == 256) tns.push_back(256);
+    else if (tm == 256) tns.push_back(256);   // 256 x 128 pairs: only when asked for (never faster)
     else tns = {256, 128};
     for (int tn : tns) {
       for (sk_mode md : modes) {
@@ -888,14 +897,22 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
 // (cached per device and variant).
 int pair_clusters(int dev, const Cfg &c, bool f32out, bool grouped) {
   static std::mutex mu;
-  static int cache[64][2][2][2][8] = {};
+  static int cache[64][2][2][2][2][16] = {};
   const int fi = c.fam == FAM_E4M3 ? 1 : 0;
-  const int st = c.stages & 7;
+  const int bi = c.BN == 128 ? 1 : 0;
+  const int st = c.stages & 15;
   std::lock_guard<std::mutex> lk(mu);
-  int &slot = cache[dev][fi][f32out][grouped][st];
+  int &slot = cache[dev][fi][bi][f32out][grouped][st];
   if (slot == 0) {
     int n = 0;
-    if (c.fam == FAM_BF16) {
+    if (c.fam == FAM_BF16 && c.BN == 128) {
+      if (grouped)
+        n = f32out ? pair_max_clusters<IN_BF16, float, 128, MAXP_GROUPED>(c.stages)
+                   : pair_max_clusters<IN_BF16, __nv_bfloat16, 128, MAXP_GROUPED>(c.stages);
+      else
+        n = f32out ? pair_max_clusters<IN_BF16, float, 128, 1>(c.stages)
+                   : pair_max_clusters<IN_BF16, __nv_bfloat16, 128, 1>(c.stages);
+    } else if (c.fam == FAM_BF16) {
       if (grouped)
         n = f32out ? pair_max_clusters<IN_BF16, float, 256, MAXP_GROUPED>(c.stages)
                    : pair_max_clusters<IN_BF16, __nv_bfloat16, 256, MAXP_GROUPED>(c.stages);

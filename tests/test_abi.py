@@ -95,10 +95,15 @@ def test_workspace_size(sk):
     c = sk.api._cfg({"num_ctas": 148, "tile_m": 128, "tile_n": 256})
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
     assert n.value == 256 + 768 + 148 * 128 * 256 * 4
-    # pairs: one 128 x 256 slot per CTA as well
-    c = sk.api._cfg({"num_ctas": 148, "tile_m": 256})
-    assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-    assert n.value == 256 + 768 + 148 * 128 * 256 * 4
+    # pairs: one 128 x tile_n slot per CTA as well
+    for tn in (256, 128):
+        c = sk.api._cfg({"num_ctas": 148, "tile_m": 256, "tile_n": tn})
+        assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+        assert n.value == 256 + 768 + 148 * 128 * tn * 4
+    # 256 x 128 pairs are BF16 only
+    q8 = sk.shape_problem(384, 384, 2048, dtype="e4m3")
+    c = sk.api._cfg({"num_ctas": 148, "tile_m": 256, "tile_n": 128})
+    assert B.sk_workspace_size(ctypes.byref(q8), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_UNSUPPORTED
     # whatever the library picks fits the default workspace (every SM, 128 x 256 slots)
     for shape in [(384, 384, 2048), (8192, 8192, 8192), (128, 8192, 16384)]:
         c = sk.api._cfg({"num_ctas": 148})

@@ -11,7 +11,7 @@ from gpu_common import assert_sampled, dev, same_strides, sk, to_np
 
 pytestmark = pytest.mark.gpu
 
-TILES = [(128, 128), (128, 256), (256, 256)]
+TILES = [(128, 128), (128, 256), (256, 128), (256, 256)]
 
 
 @pytest.fixture(scope="module")
