@@ -6,14 +6,16 @@
  *
  *     C = alpha * A * B + beta * C_in          A: m x k, B: k x n, C: m x n
  *
- * The MAC-loop iterations of all output tiles are split across one
- * persistent CTA per SM ("Stream-K", the work-centric decomposition the
- * paper studies; Introduction, Background, Methodology, after Osama et al.,
- * PPoPP 2023).  Tiles that are cut between CTAs spill FP32 partials to a
- * caller-provided workspace; the CTA that holds the tile's first k-block
- * (its owner) waits on per-CTA flags and adds the partials in ascending CTA
- * order, so the result is bit-reproducible for a fixed problem, config and
- * CTA count.  A hybrid mode computes whole tiles in data-parallel waves
+ * The MAC-loop iterations of all output tiles are split across persistent
+ * units -- one CTA, or a pair of CTAs sharing a 256-row tile, per SM or
+ * per SM pair ("Stream-K", the work-centric decomposition the paper
+ * studies; Introduction, Background, Methodology, after Osama et al.,
+ * PPoPP 2023).  Tiles that are cut between units spill FP32 partials to a
+ * caller-provided workspace; the unit that holds the tile's first k-block
+ * (its owner) waits on per-CTA flags and adds the partials in ascending unit
+ * order (or, with SK_FIXUP_LAST_ARRIVER, the last unit to arrive adds them
+ * in that same order), so the result is bit-reproducible for a fixed
+ * problem, config and unit count.  A hybrid mode computes whole tiles in data-parallel waves
  * (Background, Fig. 1) and only the ragged remainder Stream-K.  Ragged
  * M, N and K are handled without padding (Results: the padding study).
  *
