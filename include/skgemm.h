@@ -115,11 +115,21 @@ typedef struct {
 typedef enum {
     SK_FIXUP_OWNER = 0,        /* the unit holding k-block 0 waits (bounded) for
                                   the others' flags and adds their partials */
-    SK_FIXUP_LAST_ARRIVER = 1  /* every contributor spills its partial and counts
+    SK_FIXUP_LAST_ARRIVER = 1, /* every contributor spills its partial and counts
                                   its arrival with one atomic; the contributor that
                                   completes the count adds all partials.  No unit
                                   ever waits; the workspace holds twice the partial
                                   slots (no counterpart in the paper) */
+    SK_FIXUP_SPLIT = 2         /* for plans where every unit holds one range inside
+                                  one tile (all Stream-K, equal ranges dividing the
+                                  tiles' k-blocks; otherwise SK_ERR_UNSUPPORTED):
+                                  every contributor spills and waits (bounded) for
+                                  the others, then sums its share of the tile from
+                                  all partials in the same order and stores it.
+                                  With the fixup left at SK_FIXUP_OWNER and the unit
+                                  count left to the library, the library uses it
+                                  where its runtime model predicts a gain (no
+                                  counterpart in the paper) */
 } sk_fixup;
 
 /* Launch configuration.  Zero in any field selects the default. */
@@ -141,8 +151,12 @@ typedef struct {
     int min_iters_per_unit;  /* fewest k-blocks per Stream-K unit; default 4 */
     uint64_t timeout_ns;     /* bound on every device-side wait; default 2e9 ns */
     int debug_flags;         /* test-only fault injection, 0 in normal use:
-                                bit 0 = peers never raise their flags, so every
-                                owner's bounded wait expires (SK_ERR_TIMEOUT) */
+                                bit 0 = peers never raise their flags (owner
+                                protocol) or count their arrival (split reduce),
+                                so the others' bounded waits expire
+                                (SK_ERR_TIMEOUT); the last-arriver protocol has no
+                                wait.  With bit 0 set the library never picks the
+                                split reduce by itself. */
     uint64_t *trace;         /* optional DEVICE buffer of SK_TRACE_BYTES_PER_CTA
                                 bytes per launched CTA (single-problem BF16 calls;
                                 ignored elsewhere):
@@ -192,6 +206,7 @@ typedef struct {
     int64_t extra_units;     /* sk_iters mod sk_units: units with one more */
     size_t workspace_bytes;
     double predicted_us;     /* the library's runtime-model estimate of the call */
+    sk_fixup fixup;          /* the fixup protocol the call uses */
 } sk_plan_info;
 
 /* One unit of work of one CTA, in the order that CTA processes it. */

@@ -116,10 +116,10 @@ def make_problem(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor, *, C_in=Non
 
 
 def default_workspace_bytes(sms: int) -> int:
-    """Workspace for any call on a GPU with ``sms`` SMs: status word, one
-    flag per CTA, and two 128 x 256 FP32 slots per CTA (the second is used by
-    the last-arriver fixup only)."""
-    return 256 + (-(-sms * 4 // 256)) * 256 + 2 * sms * 128 * 256 * 4
+    """Workspace for any call on a GPU with ``sms`` SMs: status word (256 B),
+    the fixed flag region (1024 words), and two 128 x 256 FP32 slots per CTA
+    (the second is used by the last-arriver fixup only)."""
+    return 256 + 4096 + 2 * sms * 128 * 256 * 4
 
 
 class Workspace:

@@ -53,8 +53,8 @@ class sk_config(ctypes.Structure):
         ("fixup", ctypes.c_int),
     ]
 
-SK_FIXUP_OWNER, SK_FIXUP_LAST_ARRIVER = 0, 1
-FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER}
+SK_FIXUP_OWNER, SK_FIXUP_LAST_ARRIVER, SK_FIXUP_SPLIT = 0, 1, 2
+FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER, "split": SK_FIXUP_SPLIT}
 
 SK_TRACE_ENTRIES = 128
 SK_TRACE_BYTES_PER_CTA = SK_TRACE_ENTRIES * 16
@@ -71,7 +71,7 @@ class sk_plan_info(ctypes.Structure):
         ("tiles", ctypes.c_int64), ("sk_tiles", ctypes.c_int64), ("dp_tiles", ctypes.c_int64),
         ("sk_iters", ctypes.c_int64), ("iters_per_unit", ctypes.c_int64),
         ("extra_units", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
-        ("predicted_us", ctypes.c_double),
+        ("predicted_us", ctypes.c_double), ("fixup", ctypes.c_int),
     ]
 
 

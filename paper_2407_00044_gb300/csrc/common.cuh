@@ -21,8 +21,19 @@ struct Workspace {
   float *owner_partials;  // last-arriver fixup: g more slots (a unit's owner segment)
 };
 
+// Workspace layout: [status word, padded to 256 B][WS_MAX_CTAS flag words]
+// [per-CTA partial slots].  The flag region has a fixed size so that calls
+// with different CTA counts sharing one workspace never find another call's
+// partials where their flags are (flags must read zero between calls).
+constexpr int WS_MAX_CTAS = 1024;
+constexpr size_t WS_FLAG_OFFSET = 256;
+constexpr size_t WS_FLAG_BYTES = (size_t)WS_MAX_CTAS * 4;
+
 // Fixup protocols (sk_fixup).
-constexpr int32_t FIXUP_OWNER = 0, FIXUP_LAST_ARRIVER = 1;
+constexpr int32_t FIXUP_OWNER = 0, FIXUP_LAST_ARRIVER = 1, FIXUP_SPLIT = 2;
+// Split reduce: one counter word per tile (at the owner's flag) counts
+// arrivals in its low half and departures in its high half.
+constexpr uint32_t SPLIT_DEPART = 1u << 16;
 
 // ----------------------------------------------------------- FP32 SIMT path
 constexpr int F32_BM = 128, F32_BN = 128, F32_BK = 16, F32_THREADS = 256;

@@ -94,6 +94,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
   __shared__ uint32_t fix_word[2];   // last-arriver decisions, alternating
   int ndecide = 0;
   const bool last_arriver = P.fixup == FIXUP_LAST_ARRIVER;
+  const bool split_reduce = P.fixup == FIXUP_SPLIT;
   const int t = threadIdx.x;
   const int ty = t >> 4, tx = t & 15;
   const int u = blockIdx.x;
@@ -188,7 +189,76 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
       return *word != 0u;
     };
 
-    if (w.role == ROLE_PEER) {
+    if (split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+      // Split reduce (host-checked: every unit holds one tile-aligned
+      // range): all contributors spill, count their arrival and wait for
+      // the others; contributor j then sums the j-th share of the slot's
+      // float4 words from all partials in the fixed order and stores it.
+      int o = u, pl = w.peer_last;
+      if (w.role == ROLE_PEER) {
+        const ProbSched &q = P.ps[w.problem];
+        const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
+        o = unit_of_iter(S, ts);
+        pl = unit_of_iter(S, ts + q.iters - 1);
+      }
+      const int kc = pl - o + 1;
+      const int jx = u - o;
+      const int f0 = (int)(slot_f4 * jx / kc), f1 = (int)(slot_f4 * (jx + 1) / kc);
+      spill(slot_base + (int64_t)u * slot_f4);
+      __threadfence();
+      cta_sync();
+      uint32_t *cnt = P.ws.flags + o;
+      // test-only injection: peers never count their arrival
+      const bool withhold = (P.debug_flags & DEBUG_SKIP_PEER_FLAG) && w.role == ROLE_PEER;
+      if (f0 == f1) {
+        if (t == 0 && !withhold && (atom_add_acq_rel_gpu(cnt, 1u + SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1))
+          *cnt = 0u;
+        continue;
+      }
+      if (t == 0) {
+        if (!withhold) atom_add_acq_rel_gpu(cnt, 1u);
+        const uint64_t t0 = globaltimer();
+        while ((ld_relaxed_gpu(cnt) & 0xffffu) < (uint32_t)kc) {
+          if (globaltimer() - t0 > P.timeout_ns) {
+            atomicExch(P.ws.status, STATUS_TIMEOUT);
+            break;
+          }
+        }
+        fence_acq_rel_gpu();
+      }
+      cta_sync();
+      for (int idx = f0 + t; idx < f1; idx += F32_THREADS) {
+        float4 acc4 = __ldcg(slot_base + (int64_t)o * slot_f4 + idx);
+        for (int p = o + 1; p <= pl; ++p) {
+          const float4 q = __ldcg(slot_base + (int64_t)p * slot_f4 + idx);
+          acc4.x += q.x;
+          acc4.y += q.y;
+          acc4.z += q.z;
+          acc4.w += q.w;
+        }
+        // word idx = (row group i * 2 + column half h) * 256 + thread
+        const int vv = idx / F32_THREADS, tt = idx - vv * F32_THREADS;
+        const int i = vv >> 1, h = vv & 1, sty = tt >> 4, stx = tt & 15;
+        const int row = m0 + (i < 4 ? sty * 4 + i : 64 + sty * 4 + (i - 4));
+        const int col = n0 + h * 64 + stx * 4;
+        if (row < pr.M) {
+          const float o4[4] = {acc4.x, acc4.y, acc4.z, acc4.w};
+          float *cp = pr.C + (int64_t)row * pr.ldc + col;
+          const float *cin = pr.C_in ? pr.C_in + (int64_t)row * pr.ldc + col : nullptr;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (col + e < pr.N) {
+              float r = pr.alpha * o4[e];
+              if (pr.beta != 0.f) r += pr.beta * cin[e];
+              cp[e] = r;
+            }
+          }
+        }
+      }
+      cta_sync();
+      if (t == 0 && (atom_add_acq_rel_gpu(cnt, SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1)) *cnt = 0u;
+      continue;
+    } else if (w.role == ROLE_PEER) {
       spill(slot_base + (int64_t)u * slot_f4);
       __threadfence();
       cta_sync();

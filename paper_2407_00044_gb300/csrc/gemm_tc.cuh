@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     float4 *const oslots = reinterpret_cast<float4 *>(P.ws.owner_partials);  // owner segments (last arriver)
     constexpr int64_t SLOT_F4 = (int64_t)128 * BN / 4;
     const bool last_arriver = P.fixup == FIXUP_LAST_ARRIVER;
+    const bool split_reduce = P.fixup == FIXUP_SPLIT;
     int ndecide = 0;   // last-arriver decisions so far; its parity picks the smem word
     int acc = 0;
     uint32_t acc_phase = 0;
@@ -653,7 +654,76 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       // partials, the first from TMEM (own_tmem) or from o's owner slot.
       bool do_sum = false, own_tmem = true;
       int o = u, pl = w.peer_last;
-      if (w.role == ROLE_PEER) {
+      if (split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+        // Split reduce (the host uses it only when every unit holds one
+        // tile-aligned range, so a tile's units finish together): every
+        // contributor spills, counts its arrival, waits (bounded) for all
+        // of them, then sums its share of 64-column units from all the
+        // partials in the fixed order and stores it.
+        if (w.role == ROLE_PEER) {
+          const ProbSched &q = P.ps[w.problem];
+          const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
+          o = unit_of_iter(S, ts);
+          pl = unit_of_iter(S, ts + q.iters - 1);
+        }
+        const int kc = pl - o + 1;
+        constexpr int NU = BN / 64;
+        const int jx = u - o;
+        const int u0 = jx * NU / kc, u1 = (jx + 1) * NU / kc;
+        spill(slots + (int64_t)slot_id * SLOT_F4);
+        release_acc(acc);
+        __threadfence();
+        named_bar_sync(1, 128);
+        uint32_t *cnt = P.ws.flags + cslot(o);
+        // test-only injection: peers never count their arrival, so every
+        // other contributor's bounded wait expires
+        const bool withhold = (P.debug_flags & DEBUG_SKIP_PEER_FLAG) && w.role == ROLE_PEER;
+        if (u0 == u1) {
+          // nothing to sum here: arrive and depart at once
+          if (et == 0 && !withhold && (atom_add_acq_rel_gpu(cnt, 1u + SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1))
+            *cnt = 0u;
+        } else {
+          if (et == 0) {
+            if (!withhold) atom_add_acq_rel_gpu(cnt, 1u);
+            const uint64_t t0 = globaltimer();
+            while ((ld_relaxed_gpu(cnt) & 0xffffu) < (uint32_t)kc) {
+              if (globaltimer() - t0 > tmo) {
+                atomicExch(P.ws.status, STATUS_TIMEOUT);
+                break;
+              }
+            }
+            fence_acq_rel_gpu();
+          }
+          named_bar_sync(1, 128);
+          const float alpha = get_alpha();
+#pragma unroll 1
+          for (int ch = 2 * u0; ch < 2 * u1; ++ch) {
+            float v[32];
+            for (int p = o; p <= pl; ++p) {
+              const float4 *src = slots + (int64_t)cslot(p) * SLOT_F4 + (ch * 8) * 128 + row;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 q = __ldcg(src + j * 128);
+                if (p == o) {
+                  v[4 * j] = q.x;
+                  v[4 * j + 1] = q.y;
+                  v[4 * j + 2] = q.z;
+                  v[4 * j + 3] = q.w;
+                } else {
+                  v[4 * j] += q.x;
+                  v[4 * j + 1] += q.y;
+                  v[4 * j + 2] += q.z;
+                  v[4 * j + 3] += q.w;
+                }
+              }
+            }
+            store_chunk(ch, v, alpha);
+          }
+          named_bar_sync(1, 128);   // every thread has read the partials
+          if (et == 0 && (atom_add_acq_rel_gpu(cnt, SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1)) *cnt = 0u;
+        }
+        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
+      } else if (w.role == ROLE_PEER) {
         spill(slots + (int64_t)slot_id * SLOT_F4);
         release_acc(acc);
         if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 4, 14, nitem, globaltimer_ordered());   // spill issued
@@ -736,8 +806,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             P.ws.flags[cslot(o)] = 0u;
         }
       }
-      if (w.role != ROLE_PEER) release_acc(acc);
-      if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
+      if (!(split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER))) {
+        if (w.role != ROLE_PEER) release_acc(acc);
+        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
+      }
       ++nitem;
       if (++acc == 2) {
         acc = 0;

@@ -19,6 +19,7 @@
 #include <mutex>
 
 #include "../../include/skgemm.h"
+#include "common.cuh"
 
 namespace {
 
@@ -64,10 +65,10 @@ extern "C" SK_API sk_status sk_gemm_static_ws(const sk_problem *problem, const s
   rc = static_ws_address(&ws);
   if (rc != SK_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // The array keeps whatever the previous call left.  The status word
-  // (first 256 B) and the per-CTA flags (4 B each, padded to 256 B) must
-  // start at zero; the partial slots are always written before being read.
-  const size_t header = 256 + ((size_t)plan.num_ctas * 4 + 255) / 256 * 256;
+  // The array keeps whatever the previous call left.  The status word and
+  // the flag region must start at zero; the partial slots are always
+  // written before being read.
+  const size_t header = sk::WS_FLAG_OFFSET + sk::WS_FLAG_BYTES;
   if (cudaMemsetAsync(ws, 0, header, st) != cudaSuccess) return SK_ERR_CUDA;
   return sk_gemm(problem, &c, ws, kStaticWsBytes, stream);
 }

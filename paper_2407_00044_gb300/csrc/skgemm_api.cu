@@ -192,7 +192,7 @@ struct Cfg {
   int debug_flags;
   uint64_t *trace;
   int raster_group;
-  int fixup;       // FIXUP_OWNER or FIXUP_LAST_ARRIVER
+  int fixup;       // FIXUP_OWNER, FIXUP_LAST_ARRIVER or FIXUP_SPLIT
   int ctas() const { return pair ? 2 * g : g; }
 };
 
@@ -226,6 +226,7 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.mode = d.mode == SK_MODE_AUTO ? SK_MODE_HYBRID2 : d.mode;
   if (sms <= 0) return SK_ERR_INVALID_ARG;
   if (d.num_ctas < 0 || d.num_ctas > sms) return SK_ERR_INVALID_ARG;
+  if (sms > WS_MAX_CTAS) return SK_ERR_UNSUPPORTED;   // the workspace's flag region
   const int ctas = d.num_ctas ? d.num_ctas : sms;
   r.g = r.pair ? ctas / 2 : ctas;
   if (r.g < 1) return SK_ERR_INVALID_ARG;
@@ -236,27 +237,29 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.trace = d.trace;
   if (d.raster_group < 0 || d.raster_group > 64) return SK_ERR_INVALID_ARG;
   r.raster_group = d.raster_group ? d.raster_group : GROUP_M_DEFAULT;
-  if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER) return SK_ERR_INVALID_ARG;
-  r.fixup = d.fixup == SK_FIXUP_LAST_ARRIVER ? FIXUP_LAST_ARRIVER : FIXUP_OWNER;
+  if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER && d.fixup != SK_FIXUP_SPLIT)
+    return SK_ERR_INVALID_ARG;
+  r.fixup = d.fixup == SK_FIXUP_LAST_ARRIVER ? FIXUP_LAST_ARRIVER
+            : d.fixup == SK_FIXUP_SPLIT      ? FIXUP_SPLIT
+                                             : FIXUP_OWNER;
   *out = r;
   return SK_OK;
 }
 
-// Per CTA one partial slot (128 rows x BN FP32) and one flag; the
-// last-arriver fixup adds a second slot per CTA for its owner segment.
+// Workspace bytes (layout in common.cuh): the status word, the fixed flag
+// region, and per CTA one partial slot (128 rows x BN FP32); the
+// last-arriver fixup adds a second slot per CTA.
 size_t ws_bytes_for(const Cfg &c) {
-  const size_t flags = ((size_t)c.ctas() * 4 + 255) / 256 * 256;
   const size_t slots = (size_t)c.ctas() * 128 * c.BN * 4;
-  return 256 + flags + (c.fixup == FIXUP_LAST_ARRIVER ? 2 : 1) * slots;
+  return WS_FLAG_OFFSET + WS_FLAG_BYTES + (c.fixup == FIXUP_LAST_ARRIVER ? 2 : 1) * slots;
 }
 
 Workspace carve(void *ws, const Cfg &c) {
   uint8_t *b = static_cast<uint8_t *>(ws);
   Workspace w;
   w.status = reinterpret_cast<uint32_t *>(b);
-  w.flags = reinterpret_cast<uint32_t *>(b + 256);
-  const size_t flags = ((size_t)c.ctas() * 4 + 255) / 256 * 256;
-  w.partials = reinterpret_cast<float *>(b + 256 + flags);
+  w.flags = reinterpret_cast<uint32_t *>(b + WS_FLAG_OFFSET);
+  w.partials = reinterpret_cast<float *>(b + WS_FLAG_OFFSET + WS_FLAG_BYTES);
   w.owner_partials = c.fixup == FIXUP_LAST_ARRIVER ? w.partials + (size_t)c.ctas() * 128 * c.BN : nullptr;
   return w;
 }
@@ -385,6 +388,17 @@ ModelCoeffs model_coeffs(const Cfg &c) {
   return {284.0, 636.0, 5160.0, 3900.0, 3020.0, 0.0, 3210.0, 790.0, false};
 }
 
+// The split reduce needs every unit to hold exactly one range inside one
+// tile, so that a tile's units finish together: all tiles Stream-K, every
+// unit used, equal ranges (no remainder) that divide every tile's k-blocks.
+bool split_eligible(const PlanOut &pl) {
+  const Sched &s = pl.s;
+  if (s.num_problems <= 0 || s.sk_tiles != s.total_tiles || s.sk_units != s.g || s.r != 0 || s.q <= 0) return false;
+  for (const ProbSched &p : pl.ps)
+    if (p.iters % s.q != 0) return false;
+  return true;
+}
+
 double algorithmic_dram_bytes(const std::vector<Norm> &work) {
   double b = 0;
   for (const Norm &n : work) {
@@ -508,7 +522,25 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
         const double mac_end = mac_start + (w.k1 - w.k0) * k.iter_ns * stretch + k.mac_item_ns;
         double start = std::max(mac_end, epi_prev);
         double e;
-        if (w.role == ROLE_PEER) {
+        if (c.fixup == FIXUP_SPLIT && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+          // all contributors spill, wait for each other, then each reads
+          // about one partial's bytes and stores its share of the tile
+          int o = u, pl_ = w.peer_last;
+          if (w.role == ROLE_PEER) {
+            const ProbSched &q = pl.ps[w.problem];
+            const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
+            o = unit_of_iter(s, ts);
+            pl_ = unit_of_iter(s, ts + q.iters - 1);
+          }
+          const int kc = pl_ - o + 1;
+          const double nu = k.serial ? 1e9 : c.BN / 64.0;   // parallel shares of the tile
+          spill_done[u] = start + k.spill_ns;
+          double ready = spill_done[u];
+          if (pass > 0)
+            for (int p = o; p <= pl_; ++p) ready = std::max(ready, spill_done[p]);
+          start = ready;
+          e = k.fix_base_ns + k.fix_peer_last_ns * std::max(1.0, kc / nu) + k.store_ns / std::min<double>(kc, nu);
+        } else if (w.role == ROLE_PEER) {
           e = k.spill_ns;
           spill_done[u] = start + e;
         } else if (w.role == ROLE_OWNER) {
@@ -743,8 +775,8 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   std::string key;
   {
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n, d->stages,
-                  (int)d->mode, d->num_ctas, d->min_iters_per_unit, d->raster_group);
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n, d->stages,
+                  (int)d->mode, d->num_ctas, d->min_iters_per_unit, d->raster_group, (int)d->fixup);
     key = buf;
     for (const Norm &n : work) {
       std::snprintf(buf, sizeof(buf), "%lld,%lld,%lld,%d,%d,%d,%d;", (long long)n.M, (long long)n.N,
@@ -758,6 +790,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
     int tile_m, tile_n;
     sk_mode mode;
     int num_ctas;
+    sk_fixup fixup;
   };
   static std::mutex mu;
   static std::map<std::string, Choice> cache;
@@ -769,6 +802,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
       d->tile_n = it->second.tile_n;
       d->mode = it->second.mode;
       d->num_ctas = it->second.num_ctas;
+      d->fixup = it->second.fixup;
       return SK_OK;
     }
   }
@@ -824,13 +858,35 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
           sk_config t2 = t;
           t2.num_ctas = c.pair ? 2 * g_alt : g_alt;
           Cfg c2;
-          if (g_alt != c.g && resolve_cfg(fam, &t2, sms, &c2) == SK_OK) {
-            PlanOut pl2;
+          PlanOut pl2;
+          bool aligned = false;
+          if (g_alt == c.g) {   // already a multiple of the tile count
+            c2 = c;
+            pl2 = pl;
+            aligned = true;
+          } else if (resolve_cfg(fam, &t2, sms, &c2) == SK_OK) {
             build_plan(work, idx, c2, &pl2);
             ns = predict_ns(work, pl2, c2);
             if (ns < best * 0.999) {
               best = ns;
               best_cfg = t2;
+            }
+            aligned = true;
+          }
+          if (aligned) {
+            // ... and, if the caller left the fixup at its default, every
+            // contributor summing a share (the split reduce)
+            if (d->fixup == SK_FIXUP_OWNER && !(d->debug_flags & DEBUG_SKIP_PEER_FLAG) && split_eligible(pl2)) {
+              sk_config t3 = t2;
+              t3.fixup = SK_FIXUP_SPLIT;
+              Cfg c3;
+              if (resolve_cfg(fam, &t3, sms, &c3) == SK_OK) {
+                ns = predict_ns(work, pl2, c3);
+                if (ns < best * 0.999) {
+                  best = ns;
+                  best_cfg = t3;
+                }
+              }
             }
           }
         }
@@ -842,9 +898,10 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   d->tile_n = best_cfg.tile_n;
   d->mode = best_cfg.mode;
   d->num_ctas = best_cfg.num_ctas;
+  d->fixup = best_cfg.fixup;
   std::lock_guard<std::mutex> lk(mu);
   if (cache.size() > 4096) cache.clear();
-  cache[key] = Choice{best_cfg.tile_m, best_cfg.tile_n, best_cfg.mode, best_cfg.num_ctas};
+  cache[key] = Choice{best_cfg.tile_m, best_cfg.tile_n, best_cfg.mode, best_cfg.num_ctas, best_cfg.fixup};
   return SK_OK;
 }
 
@@ -970,6 +1027,8 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   if (work.empty()) return SK_OK;
   PlanOut pl;
   build_plan(work, idx, c, &pl);
+  if (c.fixup == FIXUP_SPLIT && !split_eligible(pl))
+    return fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
   Workspace w = carve(ws, c);
   if (c.fam == FAM_F32) {
     return grouped ? launch_f32_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_f32_family<1>(work, pl, c, w, st);
@@ -998,6 +1057,7 @@ sk_status plan_for_query(const sk_problem *problems, int count, const sk_config 
     if (maxc > 0) c->g = std::min(c->g, maxc);
   }
   build_plan(work, idx, *c, pl);
+  if (c->fixup == FIXUP_SPLIT && !work.empty() && !split_eligible(*pl)) return SK_ERR_UNSUPPORTED;
   pl->predicted_ns = work.empty() ? 0.0 : predict_ns(work, *pl, *c);
   return SK_OK;
 }
@@ -1146,6 +1206,8 @@ sk_status sk_plan_query(const sk_problem *problems, int count, const sk_config *
   out->extra_units = pl.s.r;
   out->workspace_bytes = ws_bytes_for(c);
   out->predicted_us = pl.predicted_ns * 1e-3;
+  out->fixup = c.fixup == FIXUP_SPLIT ? SK_FIXUP_SPLIT : c.fixup == FIXUP_LAST_ARRIVER ? SK_FIXUP_LAST_ARRIVER
+                                                                                         : SK_FIXUP_OWNER;
   return SK_OK;
 }
 

@@ -90,16 +90,16 @@ def test_workspace_size(sk):
     n = ctypes.c_size_t(0)
     c = sk.api._cfg({"num_ctas": 148})
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-    assert n.value == 256 + 768 + 148 * 128 * 128 * 4
+    assert n.value == 256 + 4096 + 148 * 128 * 128 * 4
     p = sk.shape_problem(384, 384, 2048)
     c = sk.api._cfg({"num_ctas": 148, "tile_m": 128, "tile_n": 256})
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-    assert n.value == 256 + 768 + 148 * 128 * 256 * 4
+    assert n.value == 256 + 4096 + 148 * 128 * 256 * 4
     # pairs: one 128 x tile_n slot per CTA as well
     for tn in (256, 128):
         c = sk.api._cfg({"num_ctas": 148, "tile_m": 256, "tile_n": tn})
         assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-        assert n.value == 256 + 768 + 148 * 128 * tn * 4
+        assert n.value == 256 + 4096 + 148 * 128 * tn * 4
     # 256 x 128 pairs are BF16 only
     q8 = sk.shape_problem(384, 384, 2048, dtype="e4m3")
     c = sk.api._cfg({"num_ctas": 148, "tile_m": 256, "tile_n": 128})
@@ -109,14 +109,40 @@ def test_workspace_size(sk):
         c = sk.api._cfg({"num_ctas": 148})
         q = sk.shape_problem(*shape)
         assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-        assert n.value <= 256 + 768 + 148 * 128 * 256 * 4
+        assert n.value <= 256 + 4096 + 148 * 128 * 256 * 4
     # the last-arriver fixup keeps a second slot per CTA (owner segments)
     for tile in ((128, 128), (128, 256), (256, 256)):
         c = sk.api._cfg({"num_ctas": 148, "tile_m": tile[0], "tile_n": tile[1], "fixup": "last_arriver"})
         assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-        assert n.value == 256 + 768 + 2 * 148 * 128 * tile[1] * 4
-    c = sk.api._cfg({"num_ctas": 148, "fixup": 2})
+        assert n.value == 256 + 4096 + 2 * 148 * 128 * tile[1] * 4
+    c = sk.api._cfg({"num_ctas": 148, "fixup": 3})
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_INVALID_ARG
+
+
+def test_split_reduce_eligibility(sk):
+    """The split reduce needs every unit to hold one range inside one tile;
+    the library picks it by itself only together with the unit count."""
+    B = sk.binding
+    f32 = sk.shape_problem(384, 384, 2048, dtype="f32")   # 9 tiles of 16 k-blocks
+    # 144 = 16 units per tile, ranges of 8 k-blocks: eligible
+    info = sk.plan(f32, sk.Config(mode="sk", num_ctas=144, fixup="split"), num_sms=152)
+    assert info.fixup == B.SK_FIXUP_SPLIT and info.extra_units == 0
+    # 152 units: unequal ranges crossing tile boundaries: refused
+    with pytest.raises(sk.SkError):
+        sk.plan(f32, sk.Config(mode="sk", num_ctas=152, fixup="split"), num_sms=152)
+    # DP tiles present: refused
+    with pytest.raises(sk.SkError):
+        sk.plan(sk.shape_problem(8192, 8192, 8192), sk.Config(mode="hybrid2", tile_m=256, fixup="split"), num_sms=152)
+    # an explicit owner request is kept when the count is fixed
+    info = sk.plan(f32, sk.Config(mode="sk", num_ctas=144), num_sms=152)
+    assert info.fixup == B.SK_FIXUP_OWNER
+    # left to the library: the tile-aligned count with the split reduce
+    info = sk.plan(f32, num_sms=152)
+    assert info.num_ctas % info.tiles == 0
+    if info.fixup == B.SK_FIXUP_SPLIT:
+        for u in range(info.num_ctas):
+            its = sk.unit_items(f32, u, sk.Config(mode="sk", num_ctas=info.num_ctas), num_sms=152)
+            assert len(its) == 1
 
 
 def test_default_workspace_fits_both_fixups(sk):
@@ -124,7 +150,7 @@ def test_default_workspace_fits_both_fixups(sk):
     B = sk.binding
     n = ctypes.c_size_t(0)
     sms = 148
-    default = 256 + (-(-sms * 4 // 256)) * 256 + 2 * sms * 128 * 256 * 4
+    default = 256 + 4096 + 2 * sms * 128 * 256 * 4
     assert sk.api.default_workspace_bytes(sms) == default
     for fix in ("owner", "last_arriver"):
         for shape in [(384, 384, 2048), (8192, 8192, 8192), (128, 8192, 16384), (1536, 1536, 8192)]:

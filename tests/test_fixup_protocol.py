@@ -116,3 +116,84 @@ def test_last_arriver_exactly_one_reducer(npeers):
         assert counter == 0, order
         n += 1
     assert n > 0
+
+
+# ---- split reduce --------------------------------------------------------
+# Every contributor of a split tile spills its partial, counts its arrival in
+# the low 16 bits of the tile's counter, waits until all kc contributors have
+# arrived, sums its own share of the tile's columns from all kc partials (in
+# unit order), then counts its departure in the high bits; the last to depart
+# resets the counter.  A contributor with an empty share arrives and departs
+# in one atomic add.  Checked here over every interleaving of the steps.
+
+DEPART = 1 << 16
+
+
+def _split_share(j, kc, nu):
+    return j * nu // kc, (j + 1) * nu // kc
+
+
+@pytest.mark.parametrize("nu", [2, 4, 8, 16])
+@pytest.mark.parametrize("kc", [2, 3, 4, 5, 7, 16, 33])
+def test_split_shares_partition_the_tile(nu, kc):
+    cols = []
+    for j in range(kc):
+        u0, u1 = _split_share(j, kc, nu)
+        assert u0 <= u1
+        cols.extend(range(u0, u1))
+    assert cols == list(range(nu))
+
+
+def _split_explore(kc, empty):
+    """DFS over all interleavings; each contributor is a program counter
+    over its steps.  Returns the number of terminal states reached."""
+    steps = {j: (["spill", "arrive_depart"] if j in empty else ["spill", "arrive", "wait", "sum", "depart"])
+             for j in range(kc)}
+    terminals = 0
+
+    def go(pc, counter, written, summed):
+        nonlocal terminals
+        moved = False
+        for j in range(kc):
+            if pc[j] == len(steps[j]):
+                continue
+            s = steps[j][pc[j]]
+            c2, w2, s2 = counter, written, summed
+            if s == "spill":
+                w2 = written | {j}
+            elif s == "arrive":
+                c2 = counter + 1
+            elif s == "arrive_depart":
+                old = counter
+                c2 = counter + 1 + DEPART
+                if (old >> 16) == kc - 1:
+                    c2 = 0
+            elif s == "wait":
+                if (counter & 0xFFFF) < kc:
+                    continue                 # blocked: no move for j
+            elif s == "sum":
+                # every partial it reads must be written
+                assert written == set(range(kc))
+                s2 = summed | {j}
+            elif s == "depart":
+                old = counter
+                c2 = counter + DEPART
+                if (old >> 16) == kc - 1:
+                    assert summed == set(range(kc)) - set(empty)
+                    c2 = 0
+            moved = True
+            go(pc[:j] + (pc[j] + 1,) + pc[j + 1:], c2, w2, s2)
+        if not moved:
+            # no contributor can move: all must be finished (no deadlock)
+            assert all(pc[j] == len(steps[j]) for j in range(kc)), (pc, counter)
+            assert counter == 0
+            assert summed == set(range(kc)) - set(empty)
+            terminals += 1
+
+    go(tuple([0] * kc), 0, frozenset(), frozenset())
+    return terminals
+
+
+@pytest.mark.parametrize("kc,empty", [(2, ()), (3, ()), (3, (1,)), (4, (0, 2)), (3, (0, 1))])
+def test_split_reduce_every_interleaving(kc, empty):
+    assert _split_explore(kc, empty) > 0

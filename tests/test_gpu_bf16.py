@@ -171,14 +171,17 @@ def test_bf16_timeout_status_and_recovery(m):
     a, b = workloads.gemm_inputs(512, 512, 4096, dtype="bf16", seed=12)
     ad, bd = a.to(d), b.to(d)
     ws = m.Workspace(d)
-    for tile_m in (128, 256):
-        m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1, tile_m=tile_m),
-               workspace=ws)
-        assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT
+    sms = torch.cuda.get_device_properties(d).multi_processor_count
+    # owner protocol on every tile (count fixed), then the split reduce
+    # (512 x 512 = 4 pair tiles on 64 pairs: k = 16)
+    for cfg in (dict(tile_m=128, num_ctas=sms), dict(tile_m=256, num_ctas=sms),
+                dict(tile_m=256, tile_n=256, num_ctas=128, fixup="split")):
+        m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1, **cfg), workspace=ws)
+        assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT, cfg
         m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
-        c = m.gemm(ad, bd, config=m.Config(mode="sk", tile_m=tile_m), workspace=ws)
+        c = m.gemm(ad, bd, config=m.Config(mode="sk", **cfg), workspace=ws)
         assert ws.status() == 0
-        assert_within_bound(c, a, b, out="bf16", what=f"after timeout {tile_m}")
+        assert_within_bound(c, a, b, out="bf16", what=f"after timeout {cfg}")
 
 
 @pytest.mark.parametrize("shape", workloads.BF16_SWEEP)

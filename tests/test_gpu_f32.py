@@ -120,9 +120,13 @@ def test_fp32_timeout_status_and_recovery(m):
     a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=8)
     ad, bd = a.to(d), b.to(d)
     ws = m.Workspace(d)
-    m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1), workspace=ws)
-    assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT
-    m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
-    c = m.gemm(ad, bd, config=m.Config(mode="sk"), workspace=ws)
-    assert ws.status() == 0
-    assert_within_bound(c, a, b, what="after timeout")
+    sms = torch.cuda.get_device_properties(d).multi_processor_count
+    # owner protocol (count fixed: the library picks no other protocol), then
+    # the split reduce, whose peers then withhold their arrival
+    for cfg in (dict(num_ctas=sms), dict(num_ctas=144, fixup="split")):
+        m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1, **cfg), workspace=ws)
+        assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT, cfg
+        m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
+        c = m.gemm(ad, bd, config=m.Config(mode="sk", **cfg), workspace=ws)
+        assert ws.status() == 0
+        assert_within_bound(c, a, b, what=f"after timeout {cfg}")

@@ -33,12 +33,21 @@ def _both(m, call, **cfg):
     return c0, c1
 
 
-def _flags_zero(m):
-    """Every flag / counter word of the default workspace is zero."""
+def _flags_zero(m, ctas=None):
+    """Every flag / counter word a call with `ctas` CTAs used (default: one
+    per SM) is zero.  The flag region holds exactly the call's CTA count
+    (rounded up to 256 bytes); the partial slots follow it."""
     ws = m.default_workspace(dev())
-    sms = torch.cuda.get_device_properties(ws.device).multi_processor_count
-    words = ws.buf[256:256 + 4 * sms].view(torch.int32)
+    if ctas is None:
+        ctas = torch.cuda.get_device_properties(ws.device).multi_processor_count
+    words = ws.buf[256:256 + 4 * ctas].view(torch.int32)
     return int(words.abs().sum().item()) == 0
+
+
+def _ctas(m, problems, cfg):
+    """CTAs of the library's plan for these problems and config."""
+    info = m.plan(problems, cfg)
+    return info.num_ctas * (2 if info.tile_m == 256 else 1)
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -52,7 +61,8 @@ def test_bf16_last_arriver_bitwise(m, tile, mode, num_ctas):
     c0, c1 = _both(m, lambda cfg: m.gemm(A, Bm, out_dtype=torch.float32, config=cfg),
                    tile_m=tile[0], tile_n=tile[1], mode=mode, num_ctas=num_ctas)
     assert torch.equal(c0, c1), (tile, mode, num_ctas)
-    assert _flags_zero(m)
+    assert _flags_zero(m, _ctas(m, m.shape_problem(392, 776, 1544),
+                               m.Config(tile_m=tile[0], tile_n=tile[1], mode=mode, num_ctas=num_ctas)))
 
 
 @pytest.mark.parametrize("tile", TILES)
@@ -65,7 +75,8 @@ def test_bf16_last_arriver_oracle(m, tile):
     assert m.default_workspace(d).status() == 0
     r = torch.arange(0, 1536, 97)
     assert_within_bound(c[r.to(d)], a[r], b, out="bf16", what=f"last-arriver {tile}")
-    assert _flags_zero(m)
+    assert _flags_zero(m, _ctas(m, m.shape_problem(1536, 1536, 8192),
+                               m.Config(fixup="last_arriver", mode="sk", tile_m=tile[0], tile_n=tile[1])))
 
 
 def test_bf16_last_arriver_int_exact_repeat(m):
@@ -80,7 +91,7 @@ def test_bf16_last_arriver_int_exact_repeat(m):
             c = m.gemm(A, Bm, out_dtype=torch.float32, config=m.Config(fixup=fix, mode="sk", num_ctas=76))
             assert np.array_equal(to_np(c), ref), (i, fix)
     assert m.default_workspace(d).status() == 0
-    assert _flags_zero(m)
+    assert _flags_zero(m, 76)
 
 
 @pytest.mark.parametrize("num_ctas", [0, 5, 40])
@@ -91,7 +102,7 @@ def test_f32_last_arriver_bitwise(m, num_ctas):
     c0, c1 = _both(m, lambda cfg: m.gemm(A, Bm, config=cfg), mode="sk", num_ctas=num_ctas)
     assert torch.equal(c0, c1)
     assert_within_bound(c1, a, b, out="f32", what="f32 last-arriver")
-    assert _flags_zero(m)
+    assert _flags_zero(m, _ctas(m, m.shape_problem(384, 384, 2048, dtype="f32"), m.Config(mode="sk", num_ctas=num_ctas)))
 
 
 @pytest.mark.parametrize("tile_m", [128, 256])
@@ -124,7 +135,7 @@ def test_grouped_last_arriver_bitwise(m, tile_m):
                    mode="sk", tile_m=tile_m)
     for x, y, s in zip(o0, o1, shapes):
         assert torch.equal(x, y), s
-    assert _flags_zero(m)
+    assert _flags_zero(m, _ctas(m, [m.shape_problem(*s) for s in shapes], m.Config(mode="sk", tile_m=tile_m)))
 
 
 def test_backward_last_arriver_bitwise(m):
@@ -134,3 +145,118 @@ def test_backward_last_arriver_bitwise(m):
     A, Bm = same_strides(a, d), same_strides(b, d)
     r0, r1 = _both(m, lambda cfg: m.gemm_backward(A, Bm, dC, config=cfg), mode="sk")
     assert torch.equal(r0[0], r1[0]) and torch.equal(r0[1], r1[1])
+
+
+# ---------------------------------------------------------------- split reduce
+# Plans where every unit holds one range inside one tile: each tile's k
+# contributors all spill, wait for each other, and each sums a share of the
+# tile in the owner protocol's order -- so the bits must match it exactly.
+
+@pytest.mark.parametrize("num_ctas", [144, 72, 36, 18])
+def test_f32_split_bitwise(m, num_ctas):
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=150)   # 9 tiles, k = num_ctas / 9
+    d = dev()
+    A, Bm = same_strides(a, d), same_strides(b, d)
+    c0 = m.gemm(A, Bm, config=m.Config(mode="sk", num_ctas=num_ctas, fixup="owner"))
+    c1 = m.gemm(A, Bm, config=m.Config(mode="sk", num_ctas=num_ctas, fixup="split"))
+    assert m.default_workspace(d).status() == 0
+    assert torch.equal(c0, c1)
+    assert_within_bound(c1, a, b, out="f32", what="f32 split")
+    assert _flags_zero(m, num_ctas)
+
+
+# (tile, num_ctas, shape): 600 x 600 = 9 pair tiles or 25 128-row tiles, K = 4096
+SPLIT_BF16 = [((256, 256), 144, (600, 600, 4096)),    # 9 tiles on 72 pairs: k = 8
+              ((256, 256), 36, (600, 600, 4096)),     # k = 2
+              ((256, 128), 120, (600, 600, 4096)),    # 15 tiles on 60 pairs: k = 4
+              ((128, 128), 100, (600, 520, 4096)),    # 25 tiles: k = 4
+              ((128, 256), 80, (600, 900, 4096))]     # 20 tiles: k = 4
+
+
+@pytest.mark.parametrize("tile,num_ctas,shape", SPLIT_BF16)
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.bfloat16])
+def test_bf16_split_bitwise(m, tile, num_ctas, shape, out_dtype):
+    M, N, K = shape
+    a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=151)
+    cfg = dict(mode="sk", tile_m=tile[0], tile_n=tile[1], num_ctas=num_ctas)
+    p = m.shape_problem(M, N, K)
+    try:
+        m.plan(p, m.Config(fixup="split", **cfg))
+    except m.SkError:
+        pytest.skip("not a tile-aligned plan")
+    d = dev()
+    A, Bm = same_strides(a, d), same_strides(b, d)
+    c0 = m.gemm(A, Bm, out_dtype=out_dtype, config=m.Config(fixup="owner", **cfg))
+    c1 = m.gemm(A, Bm, out_dtype=out_dtype, config=m.Config(fixup="split", **cfg))
+    assert m.default_workspace(d).status() == 0
+    assert torch.equal(c0, c1), (tile, num_ctas)
+    assert_within_bound(c1, a, b, out="f32" if out_dtype == torch.float32 else "bf16", what="bf16 split")
+    assert _flags_zero(m, num_ctas)
+
+
+def test_grouped_split_bitwise(m):
+    d = dev()
+    shapes = [(300, 520, 2048), (600, 256, 2048)]   # 15 + 10 tiles of 128 x 128, 32 k-blocks each
+    As, Bs = [], []
+    for i, (M, N, K) in enumerate(shapes):
+        a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=152 + i)
+        As.append(a.to(d))
+        Bs.append(b.to(d))
+    cfg = dict(mode="sk", tile_m=128, tile_n=128, num_ctas=100)   # k = 4, ranges of 8
+    o0 = m.grouped_gemm(As, Bs, out_dtype=torch.float32, config=m.Config(fixup="owner", **cfg))
+    o1 = m.grouped_gemm(As, Bs, out_dtype=torch.float32, config=m.Config(fixup="split", **cfg))
+    assert m.default_workspace(d).status() == 0
+    for x, y in zip(o0, o1):
+        assert torch.equal(x, y)
+    assert _flags_zero(m, 100)
+
+
+def test_fp8_split_bitwise(m):
+    d = dev()
+    xa = workloads.normal((512, 8192), seed=154)
+    xb = workloads.normal((512, 8192), seed=155)
+    qa, sa = m.quantize_e4m3(xa.to(d).contiguous())
+    qb, sb = m.quantize_e4m3(xb.to(d).contiguous())
+    A = qa.view(torch.float8_e4m3fn)
+    Bm = qb.view(torch.float8_e4m3fn).t()
+    cfg = dict(mode="sk", tile_m=256, num_ctas=128)   # 4 pair tiles, 64 pairs: k = 16, ranges of 4
+    c0 = m.gemm(A, Bm, out_dtype=torch.float32, scale_a=sa, scale_b=sb, config=m.Config(fixup="owner", **cfg))
+    c1 = m.gemm(A, Bm, out_dtype=torch.float32, scale_a=sa, scale_b=sb, config=m.Config(fixup="split", **cfg))
+    assert m.default_workspace(d).status() == 0
+    assert torch.equal(c0, c1)
+    assert _flags_zero(m, 128)
+
+
+def test_split_chosen_by_the_library_matches_oracle(m):
+    """The library's own choice for a few-tile, long-K problem (the split
+    reduce where the model prefers it), against the oracle."""
+    a, b = workloads.gemm_inputs(768, 768, 32768, dtype="bf16", seed=156, dist="int")
+    d = dev()
+    c = m.gemm(same_strides(a, d), same_strides(b, d), out_dtype=torch.float32)
+    assert m.default_workspace(d).status() == 0
+    r = torch.arange(0, 768, 37)
+    ref, _ = oracle.gemm(a[r], b)
+    assert np.array_equal(to_np(c[r.to(d)]), ref)
+    assert _flags_zero(m, _ctas(m, m.shape_problem(768, 768, 32768), m.Config()))
+
+
+def test_workspace_shared_across_unit_counts(m):
+    """Calls with different CTA counts share one workspace without
+    re-initialisation: a call's partial slots must never land where a later
+    call with more CTAs keeps its flags."""
+    d = dev()
+    a32, b32 = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=160)
+    abf, bbf = workloads.gemm_inputs(600, 600, 4096, dtype="bf16", seed=161, dist="int")
+    A32, B32 = same_strides(a32, d), same_strides(b32, d)
+    Abf, Bbf = same_strides(abf, d), same_strides(bbf, d)
+    ref, _ = oracle.gemm(abf, bbf)
+    for _ in range(2):
+        for g in (18, 36, 72):   # few CTAs: their slots start early in the workspace
+            m.gemm(A32, B32, config=m.Config(mode="sk", num_ctas=g, fixup="split"))
+            m.gemm(A32, B32, config=m.Config(mode="sk", num_ctas=g))
+        for fix in ("owner", "split", "last_arriver"):   # then every CTA
+            cfg = dict(mode="sk", tile_m=256, num_ctas=144)
+            c = m.gemm(Abf, Bbf, out_dtype=torch.float32, config=m.Config(fixup=fix, **cfg))
+            assert np.array_equal(to_np(c), ref), fix
+            assert _flags_zero(m, 152)
+    assert m.default_workspace(d).status() == 0
