@@ -172,7 +172,7 @@ typedef struct {
  * (c+1)*SK_TRACE_ENTRIES), each two uint64: (event << 32 | item index) and
  * %globaltimer in ns.  Entries 0..47 are written by the MMA issuer, 48..111
  * by the epilogue, 112..115 by the roles' lead threads, 116..121 by the
- * epilogue's fixup/spill detail; unused entries keep
+ * epilogue's fixup/spill/split detail; unused entries keep
  * the caller's contents (zero the buffer first). */
 #define SK_TRACE_ENTRIES 128
 #define SK_TRACE_BYTES_PER_CTA (SK_TRACE_ENTRIES * 16)
@@ -181,7 +181,8 @@ enum {
     SK_EV_MMA_BEGIN = 2,   /* item: accumulator free, MMAs about to start */
     SK_EV_MMA_END = 4,     /* item: last MMA issued and committed */
     SK_EV_EPI_BEGIN = 5,   /* item: accumulator complete, epilogue starts */
-    SK_EV_EPI_FLAGS = 6,   /* item (owner): every peer flag seen */
+    SK_EV_EPI_FLAGS = 6,   /* item (owner): every peer flag seen; split
+                              reduce: every contributor has arrived */
     SK_EV_EPI_END = 7,     /* item: epilogue done (stores issued / flag raised) */
     SK_EV_END = 8,         /* a role is done (item = 0 producer, 1 MMA issuer,
                               2 epilogue); the CTA ends at the latest of them */
@@ -189,7 +190,10 @@ enum {
     SK_EV_FIX_FIRST = 12,  /*   first staged partial chunk arrived */
     SK_EV_FIX_LAST = 13,   /*   last chunk of the first batch arrived */
     SK_EV_SPILL_ISSUED = 14,  /* peer: partial stores issued */
-    SK_EV_SPILL_VISIBLE = 15  /* peer: partial stores visible (after the fence) */
+    SK_EV_SPILL_VISIBLE = 15, /* peer (and split-reduce contributor): partial
+                                 stores visible (after the fence) */
+    SK_EV_SPLIT_SUMMED = 16   /* split reduce: this CTA's share summed and its
+                                 C stores issued */
 };
 
 /* Resolved plan of a call, for inspection and tests. */

@@ -60,7 +60,8 @@ SK_TRACE_ENTRIES = 128
 SK_TRACE_BYTES_PER_CTA = SK_TRACE_ENTRIES * 16
 TRACE_EVENTS = {1: "start", 2: "mma_begin", 4: "mma_end", 5: "epi_begin",
                 6: "epi_flags", 7: "epi_end", 8: "end", 11: "fix_issue", 12: "fix_first_data",
-                13: "fix_last_data", 14: "spill_issued", 15: "spill_visible"}
+                13: "fix_last_data", 14: "spill_issued", 15: "spill_visible",
+                16: "split_summed"}
 
 
 class sk_plan_info(ctypes.Structure):

@@ -514,10 +514,12 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         }
       };
       // Writes this CTA's accumulator rows to a workspace slot, in TMEM
-      // fragment order: float4 (chunk*8 + j)*128 + row (coalesced per warp).
-      auto spill = [&](float4 *slot) {
+      // fragment order: float4 (chunk*8 + j)*128 + row (coalesced per warp),
+      // leaving out the 32-column chunks [skip0, skip1).
+      auto spill = [&](float4 *slot, int skip0 = 0, int skip1 = 0) {
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
+          if (ch >= skip0 && ch < skip1) continue;
           float v[32];
           tmem_ld32(tbase + ch * 32, v);
 #pragma unroll
@@ -670,9 +672,12 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         constexpr int NU = BN / 64;
         const int jx = u - o;
         const int u0 = jx * NU / kc, u1 = (jx + 1) * NU / kc;
-        spill(slots + (int64_t)slot_id * SLOT_F4);
-        release_acc(acc);
+        // Only the columns the others sum leave TMEM: this CTA's own share
+        // is read back from TMEM in its place in the sum.
+        spill(slots + (int64_t)slot_id * SLOT_F4, 2 * u0, 2 * u1);
+        if (u0 == u1) release_acc(acc);
         __threadfence();
+        if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // spill visible
         named_bar_sync(1, 128);
         uint32_t *cnt = P.ws.flags + cslot(o);
         // test-only injection: peers never count their arrival, so every
@@ -693,32 +698,107 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
               }
             }
             fence_acq_rel_gpu();
+            if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           }
           named_bar_sync(1, 128);
           const float alpha = get_alpha();
-#pragma unroll 1
-          for (int ch = 2 * u0; ch < 2 * u1; ++ch) {
-            float v[32];
-            for (int p = o; p <= pl; ++p) {
-              const float4 *src = slots + (int64_t)cslot(p) * SLOT_F4 + (ch * 8) * 128 + row;
+          // Adds this CTA's own partial of chunk ch (term jx of the sum)
+          // to v, or starts v with it when it is the first term.
+          auto add_own = [&](int ch, float (&v)[32]) {
+            if (jx == 0) {
+              tmem_ld32(tbase + ch * 32, v);
+              return;
+            }
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float4 q = __ldcg(src + j * 128);
-                if (p == o) {
-                  v[4 * j] = q.x;
-                  v[4 * j + 1] = q.y;
-                  v[4 * j + 2] = q.z;
-                  v[4 * j + 3] = q.w;
-                } else {
-                  v[4 * j] += q.x;
-                  v[4 * j + 1] += q.y;
-                  v[4 * j + 2] += q.z;
-                  v[4 * j + 3] += q.w;
-                }
+            for (int j = 0; j < 4; ++j) {
+              float t8[8];
+              tmem_ld8(tbase + ch * 32 + j * 8, t8);
+#pragma unroll
+              for (int e = 0; e < 8; ++e) v[8 * j + e] += t8[e];
+            }
+          };
+          // v = q (first term) or v += q, q the 16 KB chunk image at src
+          auto add_chunk = [&](const float4 *src, bool first, bool global, float (&v)[32]) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 q = global ? __ldcg(src + j * 128) : src[j * 128];
+              if (first) {
+                v[4 * j] = q.x;
+                v[4 * j + 1] = q.y;
+                v[4 * j + 2] = q.z;
+                v[4 * j + 3] = q.w;
+              } else {
+                v[4 * j] += q.x;
+                v[4 * j + 1] += q.y;
+                v[4 * j + 2] += q.z;
+                v[4 * j + 3] += q.w;
               }
             }
-            store_chunk(ch, v, alpha);
+          };
+          // The other kc - 1 partials of this share, term ti (ascending
+          // unit, this CTA's own unit skipped) of chunk ch.
+          const int nst = kc - 1;
+          auto other = [&](int ti) { return o + ti + (ti >= jx ? 1 : 0); };
+          if (ring_free) {
+            // Stage them in the idle operand ring with 16 KB bulk copies,
+            // (chunk, term) in chunk-major order, groups of up to
+            // FIX_SMEM_UNITS copies in flight.
+            const int c0 = 2 * u0;
+            const int nunits = (2 * u1 - c0) * nst;
+            int nb = (stages * STAGE_BYTES) / FIX_UNIT_BYTES;
+            if (nb > FIX_SMEM_UNITS) nb = FIX_SMEM_UNITS;
+            float v[32];
+            int group = 0;
+            for (int g0 = 0; g0 < nunits; g0 += nb, ++group) {
+              const int gn = nunits - g0 < nb ? nunits - g0 : nb;
+              if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
+              if (et == 0) {
+                fence_proxy_async_all();   // the acquired partials, to the copy engine
+                for (int bi = 0; bi < gn; ++bi) {
+                  const int i = g0 + bi;
+                  const int ch = c0 + i / nst, ti = i % nst;
+                  const uint32_t fb = smem_u32(fix_bar + bi);
+                  mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
+                  bulk_copy_g2s(tiles_addr + bi * FIX_UNIT_BYTES,
+                                slots + (int64_t)cslot(other(ti)) * SLOT_F4 + (ch * 8) * 128, FIX_UNIT_BYTES, fb);
+                }
+              }
+              for (int bi = 0; bi < gn; ++bi) {
+                const int i = g0 + bi;
+                const int ch = c0 + i / nst, ti = i % nst;
+                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(fix_bar + bi), (uint32_t)(group & 1), tmo))) {
+                  fail();
+                  if (lane == 0) fix_fail[group & 1] = 1u;
+                  break;
+                }
+                if (tr_lead && group == 0 && bi == 0) trace_put(trace, TRACE_FIX_BASE + 1, 12, nitem, globaltimer_ordered());
+                if (tr_lead && group == 0 && bi == gn - 1) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
+                if (ti == jx) add_own(ch, v);   // own term comes before this one
+                add_chunk(reinterpret_cast<const float4 *>(smem + bi * FIX_UNIT_BYTES) + row, ti == 0 && jx != 0,
+                          false, v);
+                if (ti == nst - 1) {
+                  if (jx == kc - 1) add_own(ch, v);   // own term is the last
+                  store_chunk(ch, v, alpha);
+                }
+              }
+              named_bar_sync(1, 128);
+              if (fix_fail[group & 1] != 0u) break;
+            }
+          } else {
+#pragma unroll 1
+            for (int ch = 2 * u0; ch < 2 * u1; ++ch) {
+              float v[32];
+              for (int ti = 0; ti < nst; ++ti) {
+                if (ti == jx) add_own(ch, v);
+                add_chunk(slots + (int64_t)cslot(other(ti)) * SLOT_F4 + (ch * 8) * 128 + row, ti == 0 && jx != 0,
+                          true, v);
+              }
+              if (jx == kc - 1) add_own(ch, v);
+              store_chunk(ch, v, alpha);
+            }
           }
+          release_acc(acc);
+          if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 3, 16, nitem, globaltimer_ordered());
           named_bar_sync(1, 128);   // every thread has read the partials
           if (et == 0 && (atom_add_acq_rel_gpu(cnt, SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1)) *cnt = 0u;
         }

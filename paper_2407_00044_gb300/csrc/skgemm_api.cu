@@ -532,14 +532,19 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
             o = unit_of_iter(s, ts);
             pl_ = unit_of_iter(s, ts + q.iters - 1);
           }
+          // (tensor-core kernel: each spills all but its own share, which
+          // stays in TMEM, and reads the other kc - 1 partials of its
+          // share; FP32 kernel: each spills everything and reads kc)
           const int kc = pl_ - o + 1;
-          const double nu = k.serial ? 1e9 : c.BN / 64.0;   // parallel shares of the tile
-          spill_done[u] = start + k.spill_ns;
+          const int nu = k.serial ? 4096 : c.BN / 64;   // shares of the tile
+          const int jx = u - o;
+          const double own = (double)((jx + 1) * nu / kc - jx * nu / kc) / nu;
+          spill_done[u] = start + k.spill_ns * (k.serial ? 1.0 : 1.0 - own);
           double ready = spill_done[u];
           if (pass > 0)
             for (int p = o; p <= pl_; ++p) ready = std::max(ready, spill_done[p]);
           start = ready;
-          e = k.fix_base_ns + k.fix_peer_last_ns * std::max(1.0, kc / nu) + k.store_ns / std::min<double>(kc, nu);
+          e = own > 0 ? k.fix_base_ns + k.fix_peer_last_ns * (k.serial ? kc : kc - 1) * own + k.store_ns * own : 0.0;
         } else if (w.role == ROLE_PEER) {
           e = k.spill_ns;
           spill_done[u] = start + e;
@@ -855,39 +860,60 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
         const int64_t T = pl.s.total_tiles;
         if (d->num_ctas == 0 && pl.s.sk_tiles == T && T > 0 && 2 * T <= c.g) {
           const int g_alt = (int)(c.g / T * T);   // k = g_alt / T >= 2 units per tile
-          sk_config t2 = t;
-          t2.num_ctas = c.pair ? 2 * g_alt : g_alt;
-          Cfg c2;
-          PlanOut pl2;
-          bool aligned = false;
-          if (g_alt == c.g) {   // already a multiple of the tile count
-            c2 = c;
-            pl2 = pl;
-            aligned = true;
-          } else if (resolve_cfg(fam, &t2, sms, &c2) == SK_OK) {
-            build_plan(work, idx, c2, &pl2);
-            ns = predict_ns(work, pl2, c2);
-            if (ns < best * 0.999) {
-              best = ns;
-              best_cfg = t2;
-            }
-            aligned = true;
-          }
-          if (aligned) {
-            // ... and, if the caller left the fixup at its default, every
-            // contributor summing a share (the split reduce)
-            if (d->fixup == SK_FIXUP_OWNER && !(d->debug_flags & DEBUG_SKIP_PEER_FLAG) && split_eligible(pl2)) {
-              sk_config t3 = t2;
-              t3.fixup = SK_FIXUP_SPLIT;
-              Cfg c3;
-              if (resolve_cfg(fam, &t3, sms, &c3) == SK_OK) {
-                ns = predict_ns(work, pl2, c3);
-                if (ns < best * 0.999) {
-                  best = ns;
-                  best_cfg = t3;
+          // Tries `units` units (a multiple of T) with the owner fixup unless
+          // it is the plan already evaluated, and, if the caller left the
+          // fixup at its default, with every contributor summing a share
+          // (the split reduce) where each unit then holds one range.
+          auto try_units = [&](int units, bool owner_too) {
+            sk_config t2 = t;
+            t2.num_ctas = c.pair ? 2 * units : units;
+            Cfg c2;
+            PlanOut pl2;
+            if (units == c.g) {
+              c2 = c;
+              pl2 = pl;
+            } else {
+              if (resolve_cfg(fam, &t2, sms, &c2) != SK_OK) return;
+              build_plan(work, idx, c2, &pl2);
+              if (owner_too) {
+                const double ns2 = predict_ns(work, pl2, c2);
+                if (ns2 < best * 0.999) {
+                  best = ns2;
+                  best_cfg = t2;
                 }
               }
             }
+            if (d->fixup != SK_FIXUP_OWNER || (d->debug_flags & DEBUG_SKIP_PEER_FLAG) || !split_eligible(pl2)) return;
+            sk_config t3 = t2;
+            t3.fixup = SK_FIXUP_SPLIT;
+            Cfg c3;
+            if (resolve_cfg(fam, &t3, sms, &c3) != SK_OK) return;
+            const double ns3 = predict_ns(work, pl2, c3);
+            if (ns3 < best * 0.999) {
+              best = ns3;
+              best_cfg = t3;
+            }
+          };
+          try_units(g_alt, true);
+          // The split reduce needs the per-unit range q = (all k-blocks) /
+          // units to divide every tile's k-blocks: if g_alt misses that,
+          // the largest smaller multiple of T that meets it.
+          if (d->fixup == SK_FIXUP_OWNER && !(d->debug_flags & DEBUG_SKIP_PEER_FLAG)) {
+            int64_t total = 0;
+            for (const ProbSched &q : pl.ps) total += (int64_t)q.tiles_m * q.tiles_n * q.iters;
+            auto eligible = [&](int64_t units) {
+              if (total % units != 0) return false;
+              const int64_t qq = total / units;
+              for (const ProbSched &q : pl.ps)
+                if (q.iters % qq != 0) return false;
+              return true;
+            };
+            if (!eligible(g_alt))
+              for (int kk = (int)(g_alt / T) - 1; kk >= 2; --kk)
+                if (eligible(kk * T)) {
+                  try_units((int)(kk * T), false);
+                  break;
+                }
           }
         }
       }

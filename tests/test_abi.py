@@ -256,6 +256,26 @@ def test_tile_selection(sk):
     assert info.num_ctas == 148
 
 
+@pytest.mark.parametrize("shape", [(512, 512, 8192), (256, 256, 65536), (1280, 1280, 8192), (640, 640, 16384)])
+def test_library_split_choice_is_eligible(sk, shape):
+    """When the library picks the split reduce by itself (possibly with
+    fewer units than the largest tile-aligned count, so that the ranges
+    divide every tile's k-blocks), each unit holds exactly one range."""
+    B = sk.binding
+    p = sk.shape_problem(*shape)
+    info = sk.plan(p, num_sms=152)
+    if info.fixup != B.SK_FIXUP_SPLIT:
+        return
+    units = info.num_ctas
+    assert units % info.tiles == 0 and info.extra_units == 0
+    k = units // info.tiles
+    assert (-(-shape[2] // info.tile_k)) % k == 0
+    cfg = sk.Config(mode="sk", tile_m=info.tile_m, tile_n=info.tile_n,
+                    num_ctas=2 * units if info.tile_m == 256 else units)
+    for u in range(units):
+        assert len(sk.unit_items(p, u, cfg, num_sms=152)) == 1
+
+
 def test_tile_aligned_unit_count(sk):
     """With fewer tiles than units and the count left to the library, the
     runtime model may cut every tile into equal parts: k x T units, each
