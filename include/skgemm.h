@@ -132,6 +132,23 @@ typedef enum {
                                   counterpart in the paper) */
 } sk_fixup;
 
+/* Kernel for FP32 problems. */
+typedef enum {
+    SK_F32_AUTO = 0,       /* 3xTF32 where every problem allows it (A row-major,
+                              B column-major after normalising C to row-major,
+                              16-byte aligned bases and leading dimensions),
+                              otherwise FFMA */
+    SK_F32_FFMA = 1,       /* FP32 fused multiply-add on the SIMT pipes:
+                              128 x 128 tiles, 16-deep k-blocks */
+    SK_F32_TF32X3 = 2      /* tensor cores: each operand x = x_hi + x_lo with
+                              x_hi = tf32(x), x_lo = tf32(x - x_hi), and
+                              a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi accumulated
+                              in FP32 (dropped a_lo b_lo and the rounding of the
+                              low parts: about 2^-21 |a b| per product); 128 x
+                              128 tiles, 32-deep k-blocks, K-major operands
+                              only, else SK_ERR_UNSUPPORTED */
+} sk_f32_kernel;
+
 /* Launch configuration.  Zero in any field selects the default. */
 typedef struct {
     int tile_m;              /* 128, or 256 = CTA-pair kernel (two CTAs of a cluster
@@ -158,14 +175,15 @@ typedef struct {
                                 wait.  With bit 0 set the library never picks the
                                 split reduce by itself. */
     uint64_t *trace;         /* optional DEVICE buffer of SK_TRACE_BYTES_PER_CTA
-                                bytes per launched CTA (single-problem BF16 calls;
-                                ignored elsewhere):
+                                bytes per launched CTA (single-problem BF16 and
+                                3xTF32 calls; ignored elsewhere):
                                 each CTA records its timeline there, see
                                 SK_TRACE_* below; NULL = no tracing */
     int raster_group;        /* tile rows walked together by the rasterisation
                                 (L2 locality of concurrently running tiles);
                                 0 = default 8, at most 64 */
     sk_fixup fixup;          /* partial-sum fixup protocol; default SK_FIXUP_OWNER */
+    sk_f32_kernel f32_kernel;/* FP32 problems only; default SK_F32_AUTO */
 } sk_config;
 
 /* Timeline trace layout: CTA c owns entries [c*SK_TRACE_ENTRIES,

@@ -30,7 +30,8 @@ class Config:
     debug_flags: int = 0
     trace: int = 0          # device pointer of a timeline buffer (see trace_gemm)
     raster_group: int = 0   # rasterisation group in tile rows (0 = default)
-    fixup: str = "owner"    # "owner" (owner waits for peers) or "last_arriver"
+    fixup: str = "owner"    # "owner" (owner waits for peers), "last_arriver" or "split"
+    f32_kernel: str = "auto"   # FP32 problems: "auto", "ffma" or "tf32x3"
 
     def to_c(self) -> B.sk_config:
         c = B.sk_config()
@@ -45,6 +46,8 @@ class Config:
         c.trace = self.trace or None
         c.raster_group = self.raster_group
         c.fixup = B.FIXUP_NAMES[self.fixup] if isinstance(self.fixup, str) else int(self.fixup)
+        c.f32_kernel = (B.F32_KERNEL_NAMES[self.f32_kernel] if isinstance(self.f32_kernel, str)
+                        else int(self.f32_kernel))
         return c
 
 

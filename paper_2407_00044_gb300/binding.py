@@ -50,8 +50,11 @@ class sk_config(ctypes.Structure):
         ("mode", ctypes.c_int), ("num_ctas", ctypes.c_int),
         ("min_iters_per_unit", ctypes.c_int), ("timeout_ns", ctypes.c_uint64),
         ("debug_flags", ctypes.c_int), ("trace", ctypes.c_void_p), ("raster_group", ctypes.c_int),
-        ("fixup", ctypes.c_int),
+        ("fixup", ctypes.c_int), ("f32_kernel", ctypes.c_int),
     ]
+
+SK_F32_AUTO, SK_F32_FFMA, SK_F32_TF32X3 = 0, 1, 2
+F32_KERNEL_NAMES = {"auto": SK_F32_AUTO, "ffma": SK_F32_FFMA, "tf32x3": SK_F32_TF32X3}
 
 SK_FIXUP_OWNER, SK_FIXUP_LAST_ARRIVER, SK_FIXUP_SPLIT = 0, 1, 2
 FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER, "split": SK_FIXUP_SPLIT}

@@ -67,7 +67,9 @@ struct SimtParams {
 };
 
 // --------------------------------------------------------- tcgen05 path
-enum InKind : int { IN_BF16 = 0, IN_E4M3 = 1 };
+// IN_TF32X3: FP32 operands on the tensor cores as three TF32 products
+// (a_hi b_hi + a_hi b_lo + a_lo b_hi, x = x_hi + x_lo split in the kernel).
+enum InKind : int { IN_BF16 = 0, IN_E4M3 = 1, IN_TF32X3 = 2 };
 
 struct TcProblem {
   CUtensorMap tmap_a;   // K-major: box {BK, 128}; MN-major: box {64, BK}
@@ -120,8 +122,9 @@ __device__ __forceinline__ void trace_put(uint64_t *trace, int entry, uint32_t e
 // (32 rows x 128 bytes, 128-byte swizzled).
 constexpr int EPI_STAGE_BYTES = 4 * 2 * 4096;
 
-inline int tc_smem_bytes(int bn, int stages) {
-  const int stage = 128 * 128 + bn * 128;
+// (split_in: the 3xTF32 kernel keeps a low-part copy of every stage)
+inline int tc_smem_bytes(int bn, int stages, bool split_in = false) {
+  const int stage = (128 * 128 + bn * 128) * (split_in ? 2 : 1);
   const int need = 1024 /*alignment slack*/ + stages * stage + EPI_STAGE_BYTES + 512 /*barriers, TMEM slot*/;
   return need < 120 * 1024 ? 120 * 1024 : need;
 }

@@ -48,6 +48,14 @@ struct InTraits<IN_E4M3> {
   static constexpr uint32_t IDESC_TYPES = (1u << 4);
 };
 
+template <>
+struct InTraits<IN_TF32X3> {
+  static constexpr int BK = 32;       // 128 bytes of FP32
+  static constexpr int UMMA_K = 8;    // K of one tcgen05.mma kind::tf32
+  // D f32 (bit 4), A tf32 (bits 7-9 = 2), B tf32 (bits 10-12 = 2)
+  static constexpr uint32_t IDESC_TYPES = (1u << 4) | (2u << 7) | (2u << 10);
+};
+
 template <typename OutT>
 struct OutStore;
 
@@ -137,13 +145,18 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   constexpr int B_ROWS = PAIR ? BN / 2 : BN;    // rows of B (N direction) this CTA loads
   constexpr int A_BYTES = 128 * 128;
   constexpr int B_BYTES = B_ROWS * 128;
-  constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-  constexpr int TX_BYTES = PAIR ? 2 * STAGE_BYTES : STAGE_BYTES;   // landing on the leader's barrier
+  // 3xTF32: each stage holds the loaded operands (converted in place to
+  // their TF32 high parts) followed by their low parts.
+  constexpr bool X3 = IN == IN_TF32X3;
+  constexpr int OP_BYTES = A_BYTES + B_BYTES;
+  constexpr int STAGE_BYTES = X3 ? 2 * OP_BYTES : OP_BYTES;
+  constexpr int TX_BYTES = PAIR ? 2 * OP_BYTES : OP_BYTES;   // landing on the leader's barrier
   constexpr uint32_t TMEM_COLS = 2 * BN;
   constexpr int MN_CHUNK_BYTES = BK * 128;   // one 64-wide MN chunk of an MN-major slice
   constexpr uint32_t IDESC = Tr::IDESC_TYPES | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "tile N");
   static_assert(!PAIR || BN % 64 == 0, "pair tile N");
+  static_assert(!X3 || !PAIR, "3xTF32 runs on single CTAs");
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -158,7 +171,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *tempty_bar = tfull_bar + 2;
   uint64_t *done_bar = tempty_bar + 2;
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(fix_bar + FIX_SMEM_UNITS);
+  uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage converted (one per stage)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(conv_bar + (X3 ? stages : 0));
   volatile uint32_t *abort_flag = tmem_slot + 1;
   volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
   volatile uint32_t *fix_fail = tmem_slot + 4;   // two words: a staged-sum group failed
@@ -184,6 +198,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     }
     mbar_init(smem_u32(done_bar), 1);
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
+    if constexpr (X3)
+      for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), 4);   // the 4 epilogue warps
     *abort_flag = 0;
     fix_fail[0] = fix_fail[1] = 0;
     fence_barrier_init();
@@ -354,7 +370,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         if (TRACE && nitem < 16) trace_put(trace, tr, 2, nitem, globaltimer());
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
         for (int kb = w.k0; kb < w.k1; ++kb) {
-          if (!mbar_wait(smem_u32(full_bar + stage), phase, tmo)) {
+          // 3xTF32 waits for the epilogue warps' conversion of the stage
+          if (!mbar_wait(smem_u32((X3 ? conv_bar : full_bar) + stage), phase, tmo)) {
             ok = false;
             break;
           }
@@ -365,7 +382,14 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             const uint64_t ad = a_desc0 + soff + (uint64_t)(kk * a_kstep);
             const uint64_t bd = b_desc0 + soff + (uint64_t)(kk * b_kstep);
             const uint32_t accum = (kb > w.k0 || kk > 0) ? 1u : 0u;
-            if constexpr (PAIR) {
+            if constexpr (X3) {
+              // a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the low parts
+              // sit OP_BYTES after the high parts)
+              constexpr uint64_t LO = (uint64_t)(OP_BYTES >> 4);
+              mma_tf32(d_tmem, ad, bd, idesc, accum);
+              mma_tf32(d_tmem, ad, bd + LO, idesc, 1u);
+              mma_tf32(d_tmem, ad + LO, bd, idesc, 1u);
+            } else if constexpr (PAIR) {
               if constexpr (IN == IN_BF16)
                 mma_f16_pair(d_tmem, ad, bd, idesc, accum);
               else
@@ -445,8 +469,40 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     // threads: the lanes of a warp must stay converged for the
     // warp-collective tcgen05.ld, and all four warps must reach the same
     // named barriers.
+    int cstage = 0;          // 3xTF32: next stage to convert and its phase
+    uint32_t cphase = 0;
     while (cursor_next(S, P.ps, u, c, w)) {
       const TcProblem &pr = P.prob[w.problem];
+      if constexpr (X3) {
+        // Split every loaded FP32 value x of the item's stages into
+        // x_hi = tf32(x), written over x, and x_lo = tf32(x - x_hi), written
+        // OP_BYTES further on (x - x_hi is exact in FP32); then hand the
+        // stage to the MMA issuer.  The operation is elementwise, so the
+        // swizzled layout is kept as TMA wrote it.
+        for (int kb = w.k0; kb < w.k1; ++kb) {
+          if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(full_bar + cstage), cphase, tmo)) || *abort_flag) {
+            if (lane == 0) fail();
+            break;
+          }
+          float4 *x = reinterpret_cast<float4 *>(smem + cstage * STAGE_BYTES);
+          float4 *lo = x + OP_BYTES / 16;
+#pragma unroll 4
+          for (int i = et; i < OP_BYTES / 16; i += 128) {
+            const float4 v = x[i];
+            const float4 h = make_float4(round_tf32(v.x), round_tf32(v.y), round_tf32(v.z), round_tf32(v.w));
+            x[i] = h;
+            lo[i] = make_float4(round_tf32(v.x - h.x), round_tf32(v.y - h.y), round_tf32(v.z - h.z),
+                                round_tf32(v.w - h.w));
+          }
+          fence_proxy_async_smem_cta();   // the generic writes, to the tensor cores' reads
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(conv_bar + cstage));
+          if (++cstage == stages) {
+            cstage = 0;
+            cphase ^= 1u;
+          }
+        }
+      }
       const bool got = mbar_wait(smem_u32(tfull_bar + acc), acc_phase, tmo);
       if (named_bar_or(1, 128, !got || *abort_flag != 0u)) {
         if (!got) fail();
@@ -513,20 +569,24 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           if (gcol < pr.N) OutStore<OutT>::run(pr, grow, gcol, v, alpha);
         }
       };
-      // Writes this CTA's accumulator rows to a workspace slot, in TMEM
-      // fragment order: float4 (chunk*8 + j)*128 + row (coalesced per warp),
-      // leaving out the 32-column chunks [skip0, skip1).
-      auto spill = [&](float4 *slot, int skip0 = 0, int skip1 = 0) {
+      // Writes this CTA's accumulator rows to a workspace slot in TMEM
+      // fragment order: float4 ((chunk*4 + q4)*8 + j)*32 + lane, so a warp
+      // writes 512 contiguous bytes per store, a 32-column chunk of all
+      // rows is one 16 KB block and a warp's 32 rows of it one 4 KB block.
+      // Leaves out the chunks for which skip(ch) holds.
+      auto spill = [&](float4 *slot, auto skip) {
 #pragma unroll 1
         for (int ch = 0; ch < BN / 32; ++ch) {
-          if (ch >= skip0 && ch < skip1) continue;
+          if (skip(ch)) continue;
           float v[32];
           tmem_ld32(tbase + ch * 32, v);
 #pragma unroll
           for (int j = 0; j < 8; ++j)
-            __stcg(slot + (ch * 8 + j) * 128 + row, make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+            __stcg(slot + ((ch * 4 + q4) * 8 + j) * 32 + lane,
+                   make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         }
       };
+      auto no_skip = [](int) { return false; };
       // Sums the partials of a tile whose k-blocks units o..pl computed, in
       // the fixed order: unit o's partial (k-block 0; from this CTA's TMEM
       // if own_in_tmem, else from o's owner slot), then units o+1..pl
@@ -581,7 +641,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
               if (ti == 0 && !own_in_tmem) {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                  const float4 q = sb[j * 128 + row];
+                  const float4 q = sb[(q4 * 8 + j) * 32 + lane];
                   v[4 * j] = q.x;
                   v[4 * j + 1] = q.y;
                   v[4 * j + 2] = q.z;
@@ -591,7 +651,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                 if (ti == 0) tmem_ld32(tbase + ch * 32, v);
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                  const float4 q = sb[j * 128 + row];
+                  const float4 q = sb[(q4 * 8 + j) * 32 + lane];
                   v[4 * j] += q.x;
                   v[4 * j + 1] += q.y;
                   v[4 * j + 2] += q.z;
@@ -617,10 +677,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             if (own_in_tmem) {
               tmem_ld32(tbase + ch * 32, v);
             } else {
-              const float4 *src = src_of(ch, 0) + row;
+              const float4 *src = src_of(ch, 0) + q4 * 256 + lane;
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                const float4 q = __ldcg(src + j * 128);
+                const float4 q = __ldcg(src + j * 32);
                 v[4 * j] = q.x;
                 v[4 * j + 1] = q.y;
                 v[4 * j + 2] = q.z;
@@ -628,10 +688,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
               }
             }
             for (int ti = own_in_tmem ? 0 : 1; ti < nst; ++ti) {
-              const float4 *src = src_of(ch, ti) + row;
+              const float4 *src = src_of(ch, ti) + q4 * 256 + lane;
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                const float4 q = __ldcg(src + j * 128);
+                const float4 q = __ldcg(src + j * 32);
                 v[4 * j] += q.x;
                 v[4 * j + 1] += q.y;
                 v[4 * j + 2] += q.z;
@@ -659,9 +719,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       if (split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
         // Split reduce (the host uses it only when every unit holds one
         // tile-aligned range, so a tile's units finish together): every
-        // contributor spills, counts its arrival, waits (bounded) for all
-        // of them, then sums its share of 64-column units from all the
-        // partials in the fixed order and stores it.
+        // contributor spills what the others sum, counts its arrival, waits
+        // (bounded) for all of them; then each of its warps sums its units
+        // from all the partials in the fixed order and stores them.
         if (w.role == ROLE_PEER) {
           const ProbSched &q = P.ps[w.problem];
           const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
@@ -669,13 +729,23 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           pl = unit_of_iter(S, ts + q.iters - 1);
         }
         const int kc = pl - o + 1;
-        constexpr int NU = BN / 64;
         const int jx = u - o;
-        const int u0 = jx * NU / kc, u1 = (jx + 1) * NU / kc;
-        // Only the columns the others sum leave TMEM: this CTA's own share
-        // is read back from TMEM in its place in the sum.
-        spill(slots + (int64_t)slot_id * SLOT_F4, 2 * u0, 2 * u1);
-        if (u0 == u1) release_acc(acc);
+        // A unit is UW chunks (64 columns for BF16 output, the width of its
+        // TMA store box; 32 for FP32) of one warp's 32 rows; unit s covers
+        // chunk group s / 4 of warp s % 4, and contributor jx takes units
+        // [s0, s1), so consecutive units go to different warps.
+        constexpr int UW = sizeof(OutT) == 4 ? 1 : 2;
+        constexpr int NS = 4 * (BN / 32) / UW;
+        const int s0 = jx * NS / kc, s1 = (jx + 1) * NS / kc;
+        const int s_first = s0 + ((q4 - s0 % 4) + 4) % 4;   // this warp's first unit
+        const int nunit_w = s_first < s1 ? (s1 - 1 - s_first) / 4 + 1 : 0;
+        // This warp's own units stay in TMEM and enter the sum in their
+        // place; the rest of its rows go to the workspace.
+        spill(slots + (int64_t)slot_id * SLOT_F4, [&](int ch) {
+          const int su = (ch / UW) * 4 + q4;
+          return su >= s0 && su < s1;
+        });
+        if (nunit_w == 0) release_acc(acc);
         __threadfence();
         if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // spill visible
         named_bar_sync(1, 128);
@@ -683,7 +753,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         // test-only injection: peers never count their arrival, so every
         // other contributor's bounded wait expires
         const bool withhold = (P.debug_flags & DEBUG_SKIP_PEER_FLAG) && w.role == ROLE_PEER;
-        if (u0 == u1) {
+        if (s0 == s1) {
           // nothing to sum here: arrive and depart at once
           if (et == 0 && !withhold && (atom_add_acq_rel_gpu(cnt, 1u + SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1))
             *cnt = 0u;
@@ -701,110 +771,113 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           }
           named_bar_sync(1, 128);
-          const float alpha = get_alpha();
-          // Adds this CTA's own partial of chunk ch (term jx of the sum)
-          // to v, or starts v with it when it is the first term.
-          auto add_own = [&](int ch, float (&v)[32]) {
-            if (jx == 0) {
-              tmem_ld32(tbase + ch * 32, v);
-              return;
-            }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              float t8[8];
-              tmem_ld8(tbase + ch * 32 + j * 8, t8);
-#pragma unroll
-              for (int e = 0; e < 8; ++e) v[8 * j + e] += t8[e];
-            }
-          };
-          // v = q (first term) or v += q, q the 16 KB chunk image at src
-          auto add_chunk = [&](const float4 *src, bool first, bool global, float (&v)[32]) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 q = global ? __ldcg(src + j * 128) : src[j * 128];
-              if (first) {
-                v[4 * j] = q.x;
-                v[4 * j + 1] = q.y;
-                v[4 * j + 2] = q.z;
-                v[4 * j + 3] = q.w;
-              } else {
-                v[4 * j] += q.x;
-                v[4 * j + 1] += q.y;
-                v[4 * j + 2] += q.z;
-                v[4 * j + 3] += q.w;
+          if (nunit_w > 0) {
+            const float alpha = get_alpha();
+            // Adds this CTA's own partial of chunk ch (term jx of the sum)
+            // to v, or starts v with it when it is the first term.
+            auto add_own = [&](int ch, float (&v)[32]) {
+              if (jx == 0) {
+                tmem_ld32(tbase + ch * 32, v);
+                return;
               }
-            }
-          };
-          // The other kc - 1 partials of this share, term ti (ascending
-          // unit, this CTA's own unit skipped) of chunk ch.
-          const int nst = kc - 1;
-          auto other = [&](int ti) { return o + ti + (ti >= jx ? 1 : 0); };
-          if (ring_free) {
-            // Stage them in the idle operand ring with 16 KB bulk copies,
-            // (chunk, term) in chunk-major order, groups of up to
-            // FIX_SMEM_UNITS copies in flight.
-            const int c0 = 2 * u0;
-            const int nunits = (2 * u1 - c0) * nst;
-            int nb = (stages * STAGE_BYTES) / FIX_UNIT_BYTES;
-            if (nb > FIX_SMEM_UNITS) nb = FIX_SMEM_UNITS;
-            float v[32];
-            int group = 0;
-            for (int g0 = 0; g0 < nunits; g0 += nb, ++group) {
-              const int gn = nunits - g0 < nb ? nunits - g0 : nb;
-              if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
-              if (et == 0) {
-                fence_proxy_async_all();   // the acquired partials, to the copy engine
-                for (int bi = 0; bi < gn; ++bi) {
-                  const int i = g0 + bi;
-                  const int ch = c0 + i / nst, ti = i % nst;
-                  const uint32_t fb = smem_u32(fix_bar + bi);
-                  mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
-                  bulk_copy_g2s(tiles_addr + bi * FIX_UNIT_BYTES,
-                                slots + (int64_t)cslot(other(ti)) * SLOT_F4 + (ch * 8) * 128, FIX_UNIT_BYTES, fb);
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                float t8[8];
+                tmem_ld8(tbase + ch * 32 + j * 8, t8);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) v[8 * j + e] += t8[e];
+              }
+            };
+            // v = q (first term) or v += q, q this warp's 4 KB block image
+            auto add_block = [&](const float4 *blk, bool first, bool global, float (&v)[32]) {
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 q = global ? __ldcg(blk + j * 32 + lane) : blk[j * 32 + lane];
+                if (first) {
+                  v[4 * j] = q.x;
+                  v[4 * j + 1] = q.y;
+                  v[4 * j + 2] = q.z;
+                  v[4 * j + 3] = q.w;
+                } else {
+                  v[4 * j] += q.x;
+                  v[4 * j + 1] += q.y;
+                  v[4 * j + 2] += q.z;
+                  v[4 * j + 3] += q.w;
                 }
               }
-              for (int bi = 0; bi < gn; ++bi) {
-                const int i = g0 + bi;
-                const int ch = c0 + i / nst, ti = i % nst;
-                if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(fix_bar + bi), (uint32_t)(group & 1), tmo))) {
-                  fail();
-                  if (lane == 0) fix_fail[group & 1] = 1u;
+            };
+            // The other kc - 1 partials: term ti (ascending unit, this
+            // CTA's own unit skipped); piece i = (chunk i / nst of this
+            // warp's chunks, term i % nst).
+            const int nst = kc - 1;
+            auto other = [&](int ti) { return o + ti + (ti >= jx ? 1 : 0); };
+            auto chunk_of = [&](int k) { return ((s_first + 4 * (k / UW)) / 4) * UW + k % UW; };
+            auto block_of = [&](int ch, int ti) {
+              return slots + (int64_t)cslot(other(ti)) * SLOT_F4 + (ch * 4 + q4) * 256;
+            };
+            const int npieces = nunit_w * UW * nst;
+            if (ring_free) {
+              // Stage the pieces in this warp's quarter of the idle operand
+              // ring with 4 KB bulk copies, a group at a time on one barrier.
+              constexpr int PIECE = 4096;
+              int nb = (stages * STAGE_BYTES / 4) / PIECE;
+              const uint32_t wbase = tiles_addr + (uint32_t)(q4 * (stages * STAGE_BYTES / 4));
+              const float4 *wsmem = reinterpret_cast<const float4 *>(smem + q4 * (stages * STAGE_BYTES / 4));
+              const uint32_t fb = smem_u32(fix_bar + q4);
+              float v[32];
+              int group = 0;
+              bool okw = true;
+              for (int g0 = 0; g0 < npieces && okw; g0 += nb, ++group) {
+                const int gn = npieces - g0 < nb ? npieces - g0 : nb;
+                __syncwarp();   // the previous group's images are consumed
+                if (lane == 0) {
+                  fence_proxy_async_all();   // the acquired partials, to the copy engine
+                  mbar_arrive_expect_tx(fb, (uint32_t)(gn * PIECE));
+                  for (int bi = 0; bi < gn; ++bi) {
+                    const int i = g0 + bi;
+                    bulk_copy_g2s(wbase + bi * PIECE, block_of(chunk_of(i / nst), i % nst), PIECE, fb);
+                  }
+                }
+                if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
+                if (!__all_sync(0xffffffffu, mbar_wait(fb, (uint32_t)(group & 1), tmo))) {
+                  if (lane == 0) fail();
+                  okw = false;
                   break;
                 }
-                if (tr_lead && group == 0 && bi == 0) trace_put(trace, TRACE_FIX_BASE + 1, 12, nitem, globaltimer_ordered());
-                if (tr_lead && group == 0 && bi == gn - 1) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
-                if (ti == jx) add_own(ch, v);   // own term comes before this one
-                add_chunk(reinterpret_cast<const float4 *>(smem + bi * FIX_UNIT_BYTES) + row, ti == 0 && jx != 0,
-                          false, v);
-                if (ti == nst - 1) {
-                  if (jx == kc - 1) add_own(ch, v);   // own term is the last
-                  store_chunk(ch, v, alpha);
+                if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
+                for (int bi = 0; bi < gn; ++bi) {
+                  const int i = g0 + bi;
+                  const int ch = chunk_of(i / nst), ti = i % nst;
+                  if (ti == jx) add_own(ch, v);   // own term comes before this one
+                  add_block(wsmem + bi * (PIECE / 16), ti == 0 && jx != 0, false, v);
+                  if (ti == nst - 1) {
+                    if (jx == kc - 1) add_own(ch, v);   // own term is the last
+                    store_chunk(ch, v, alpha);
+                  }
                 }
               }
-              named_bar_sync(1, 128);
-              if (fix_fail[group & 1] != 0u) break;
-            }
-          } else {
+            } else {
 #pragma unroll 1
-            for (int ch = 2 * u0; ch < 2 * u1; ++ch) {
-              float v[32];
-              for (int ti = 0; ti < nst; ++ti) {
-                if (ti == jx) add_own(ch, v);
-                add_chunk(slots + (int64_t)cslot(other(ti)) * SLOT_F4 + (ch * 8) * 128 + row, ti == 0 && jx != 0,
-                          true, v);
+              for (int k = 0; k < nunit_w * UW; ++k) {
+                const int ch = chunk_of(k);
+                float v[32];
+                for (int ti = 0; ti < nst; ++ti) {
+                  if (ti == jx) add_own(ch, v);
+                  add_block(block_of(ch, ti), ti == 0 && jx != 0, true, v);
+                }
+                if (jx == kc - 1) add_own(ch, v);
+                store_chunk(ch, v, alpha);
               }
-              if (jx == kc - 1) add_own(ch, v);
-              store_chunk(ch, v, alpha);
             }
+            release_acc(acc);
           }
-          release_acc(acc);
           if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 3, 16, nitem, globaltimer_ordered());
           named_bar_sync(1, 128);   // every thread has read the partials
           if (et == 0 && (atom_add_acq_rel_gpu(cnt, SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1)) *cnt = 0u;
         }
         if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       } else if (w.role == ROLE_PEER) {
-        spill(slots + (int64_t)slot_id * SLOT_F4);
+        spill(slots + (int64_t)slot_id * SLOT_F4, no_skip);
         release_acc(acc);
         if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 4, 14, nitem, globaltimer_ordered());   // spill issued
         __threadfence();
@@ -856,7 +929,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           }
           do_sum = broadcast(mine);
           if (!do_sum) {
-            spill(oslots + (int64_t)slot_id * SLOT_F4);
+            spill(oslots + (int64_t)slot_id * SLOT_F4, no_skip);
             __threadfence();
             named_bar_sync(1, 128);
             if (et == 0) mine = atom_add_acq_rel_gpu(P.ws.flags + slot_id, 1u) == npeers;
@@ -926,7 +999,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool TRACE>
 cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
   auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, TRACE>;
-  const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages);
+  const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages, IN == IN_TF32X3);
   (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -952,11 +1025,11 @@ cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st
   }
 }
 
-// Tracing variants exist for single-problem BF16 launches; elsewhere a
-// trace buffer is ignored.
+// Tracing variants exist for single-problem BF16 and 3xTF32 launches;
+// elsewhere a trace buffer is ignored.
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
 cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  if constexpr (IN == IN_BF16 && MAXP == 1) {
+  if constexpr ((IN == IN_BF16 || IN == IN_TF32X3) && MAXP == 1) {
     if (p.trace) return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true>(p, grid, st);
   }
   return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, false>(p, grid, st);

@@ -1,0 +1,8 @@
+// FP32-input instantiations of the tcgen05 Stream-K kernel (3xTF32).
+#include "gemm_tc.cuh"
+
+namespace sk {
+template cudaError_t launch_tc<IN_TF32X3, float, 128, 1, false>(const TcParams<1> &, int, cudaStream_t);
+template cudaError_t launch_tc<IN_TF32X3, float, 128, MAXP_GROUPED, false>(const TcParams<MAXP_GROUPED> &, int,
+                                                                           cudaStream_t);
+}  // namespace sk

@@ -193,6 +193,7 @@ struct Cfg {
   uint64_t *trace;
   int raster_group;
   int fixup;       // FIXUP_OWNER, FIXUP_LAST_ARRIVER or FIXUP_SPLIT
+  bool tc32 = false;   // FP32 on the tensor cores (3xTF32) instead of FFMA
   int ctas() const { return pair ? 2 * g : g; }
 };
 
@@ -205,7 +206,19 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   if (d.tile_m != 128 && d.tile_m != 256) return SK_ERR_UNSUPPORTED;   // 0 was resolved by auto_tile
   r.pair = d.tile_m == 256;
   r.BM = d.tile_m;
-  if (fam == FAM_F32) {
+  if (d.f32_kernel < SK_F32_AUTO || d.f32_kernel > SK_F32_TF32X3) return SK_ERR_INVALID_ARG;
+  if (fam == FAM_F32 && d.f32_kernel == SK_F32_TF32X3) {
+    // 3xTF32 on the tensor cores: 128 x 128 tiles, 32-deep k-blocks, each
+    // stage twice the loaded bytes (high and low parts)
+    if (r.pair) return SK_ERR_UNSUPPORTED;
+    if (d.tile_n != 0 && d.tile_n != 128) return SK_ERR_UNSUPPORTED;
+    r.tc32 = true;
+    r.BN = 128;
+    r.BK = 32;
+    const int max_stages = (227 * 1024 - 1024 - 512 - EPI_STAGE_BYTES) / (2 * (128 * 128 + 128 * 128));
+    r.stages = d.stages ? d.stages : max_stages;
+    if (r.stages < 2 || r.stages > max_stages) return SK_ERR_UNSUPPORTED;
+  } else if (fam == FAM_F32) {
     if (r.pair) return SK_ERR_UNSUPPORTED;
     if (d.tile_n != 0 && d.tile_n != 128) return SK_ERR_UNSUPPORTED;
     r.BN = 128;
@@ -367,6 +380,11 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // operands per 256-cycle k-block, beyond what L2 delivers to one SM, so a
 // k-block costs about what a 256 x 256 one does (measured 8192^3: 986 us).
 #define PAIR128_COEFFS 520.0, 1190.0, 5270.0, 4000.0, 3500.0, 0.0, 2600.0, 3000.0
+// 3xTF32 (128 x 128 tiles, 32-deep k-blocks: three TF32 MMAs of half the
+// BF16 rate per k-block plus the in-kernel split of the stage; the
+// epilogue warps also do the split, so an epilogue does not overlap the
+// next item's MMAs).
+#define TF32X3_COEFFS 430.0, 900.0, 5160.0, 4500.0, 3020.0, 0.0, 3210.0, 790.0
 
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
@@ -381,6 +399,7 @@ struct ModelCoeffs {
 };
 
 ModelCoeffs model_coeffs(const Cfg &c) {
+  if (c.fam == FAM_F32 && c.tc32) return {TF32X3_COEFFS, false};
   if (c.fam == FAM_F32) return {1700.0, 500.0, 6000.0, 1000.0, 2000.0, 1000.0, 1000.0, 1000.0, true};
   if (c.pair && c.BN == 128) return {PAIR128_COEFFS, false};
   if (c.pair) return {302.0, 1190.0, 5270.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0, false};
@@ -532,19 +551,31 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
             o = unit_of_iter(s, ts);
             pl_ = unit_of_iter(s, ts + q.iters - 1);
           }
-          // (tensor-core kernel: each spills all but its own share, which
-          // stays in TMEM, and reads the other kc - 1 partials of its
-          // share; FP32 kernel: each spills everything and reads kc)
+          // (tensor-core kernel: the tile's columns x row quarters are cut
+          // into NS units dealt out in order, a unit's partials summed by
+          // one warp; each contributor spills all but its own units, which
+          // stay in TMEM, and its busiest warp reads the other kc - 1
+          // partials of its units.  FP32 FFMA kernel: each spills
+          // everything and reads kc partials of its share.)
           const int kc = pl_ - o + 1;
-          const int nu = k.serial ? 4096 : c.BN / 64;   // shares of the tile
           const int jx = u - o;
-          const double own = (double)((jx + 1) * nu / kc - jx * nu / kc) / nu;
-          spill_done[u] = start + k.spill_ns * (k.serial ? 1.0 : 1.0 - own);
+          double own_cta, own_warp;
+          if (k.serial) {
+            own_cta = own_warp = (double)((jx + 1) * 4096 / kc - jx * 4096 / kc) / 4096;
+          } else {
+            const int ns = 4 * (c.BN / 32) / (work[w.problem].c_type == SK_F32 ? 1 : 2);
+            const int n_u = (jx + 1) * ns / kc - jx * ns / kc;
+            own_cta = (double)n_u / ns;
+            own_warp = (double)((n_u + 3) / 4) / (ns / 4);
+          }
+          spill_done[u] = start + k.spill_ns * (k.serial ? 1.0 : 1.0 - own_cta);
           double ready = spill_done[u];
           if (pass > 0)
             for (int p = o; p <= pl_; ++p) ready = std::max(ready, spill_done[p]);
           start = ready;
-          e = own > 0 ? k.fix_base_ns + k.fix_peer_last_ns * (k.serial ? kc : kc - 1) * own + k.store_ns * own : 0.0;
+          e = own_cta > 0
+                  ? k.fix_base_ns + k.fix_peer_last_ns * (k.serial ? kc : kc - 1) * own_warp + k.store_ns * own_warp
+                  : 0.0;
         } else if (w.role == ROLE_PEER) {
           e = k.spill_ns;
           spill_done[u] = start + e;
@@ -577,7 +608,8 @@ sk_status check_tc_alignment(const Norm &n) {
   const int es = dtype_bytes(n.in_type);
   if (!aligned16(n.A) || !aligned16(n.B)) return SK_ERR_UNSUPPORTED;
   if ((n.lda * es) % 16 != 0 || (n.ldb * es) % 16 != 0) return SK_ERR_UNSUPPORTED;
-  if (n.in_type == SK_E4M3 && (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR)) return SK_ERR_UNSUPPORTED;
+  if ((n.in_type == SK_E4M3 || n.in_type == SK_F32) && (n.a_layout != SK_ROW_MAJOR || n.b_layout != SK_COL_MAJOR))
+    return SK_ERR_UNSUPPORTED;
   return SK_OK;
 }
 
@@ -591,7 +623,9 @@ sk_status check_pair_layout(const Norm &n) {
 sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk_dtype t, bool kmajor, int64_t rows,
                          int64_t K, int64_t ld, int box_rows, int BK) {
   const int es = dtype_bytes(t);
-  const CUtensorMapDataType dt = t == SK_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUtensorMapDataType dt = t == SK_BF16  ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : t == SK_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                               : CU_TENSOR_MAP_DATA_TYPE_UINT8;
   cuuint64_t dims[2], strides[1];
   cuuint32_t box[2], estr[2] = {1, 1};
   if (kmajor) {   // element (r, k) at base[r*ld + k]
@@ -693,6 +727,8 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
     else
       e = f32out ? launch_tc<IN_BF16, float, 128, MAXP, false>(*P, pl.grid, st)
                  : launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP, false>(*P, pl.grid, st);
+  } else if (c.fam == FAM_F32) {
+    e = launch_tc<IN_TF32X3, float, 128, MAXP, false>(*P, pl.grid, st);
   } else if (c.fam == FAM_E4M3) {
     if constexpr (MAXP == 1) {
       if (c.pair)
@@ -780,8 +816,9 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   std::string key;
   {
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n, d->stages,
-                  (int)d->mode, d->num_ctas, d->min_iters_per_unit, d->raster_group, (int)d->fixup);
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n,
+                  d->stages, (int)d->mode, d->num_ctas, d->min_iters_per_unit, d->raster_group, (int)d->fixup,
+                  (int)d->f32_kernel, d->debug_flags & DEBUG_SKIP_PEER_FLAG);
     key = buf;
     for (const Norm &n : work) {
       std::snprintf(buf, sizeof(buf), "%lld,%lld,%lld,%d,%d,%d,%d;", (long long)n.M, (long long)n.N,
@@ -959,12 +996,19 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
   sk_config d;
   std::memset(&d, 0, sizeof(d));
   if (cfg) d = *cfg;
+  if (fam == FAM_F32 && d.f32_kernel == SK_F32_AUTO) {
+    // 3xTF32 where every problem's operands suit TMA and the K-major
+    // descriptors; FFMA otherwise
+    bool tc_ok = true;
+    for (const Norm &n : *work) tc_ok = tc_ok && check_tc_alignment(n) == SK_OK;
+    d.f32_kernel = tc_ok ? SK_F32_TF32X3 : SK_F32_FFMA;
+  }
   sk_status rc = choose_auto(fam, *work, *idx, sms, &d);
   if (rc != SK_OK) return rc;
   rc = resolve_cfg(fam, &d, sms, c);
   if (rc != SK_OK) return rc;
   for (const Norm &n : *work) {
-    if (fam != FAM_F32) {
+    if (fam != FAM_F32 || c->tc32) {
       rc = check_tc_alignment(n);
       if (rc != SK_OK) return rc;
     }
@@ -1056,7 +1100,7 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   if (c.fixup == FIXUP_SPLIT && !split_eligible(pl))
     return fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
   Workspace w = carve(ws, c);
-  if (c.fam == FAM_F32) {
+  if (c.fam == FAM_F32 && !c.tc32) {
     return grouped ? launch_f32_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_f32_family<1>(work, pl, c, w, st);
   }
   return grouped ? launch_tc_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_tc_family<1>(work, pl, c, w, st);

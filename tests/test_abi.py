@@ -276,6 +276,27 @@ def test_library_split_choice_is_eligible(sk, shape):
         assert len(sk.unit_items(p, u, cfg, num_sms=152)) == 1
 
 
+def test_f32_kernel_choice(sk):
+    """FP32 problems go to the 3xTF32 tensor-core kernel (32-deep k-blocks)
+    when both operands are K-major and TMA-aligned, else to the FFMA
+    kernel (16-deep); an explicit 3xTF32 request on other layouts is
+    refused, an unknown kernel value is invalid."""
+    B = sk.binding
+    kmaj = sk.shape_problem(384, 384, 2048, dtype="f32")
+    assert sk.plan(kmaj, num_sms=152).tile_k == 32
+    assert sk.plan(kmaj, sk.Config(f32_kernel="ffma"), num_sms=152).tile_k == 16
+    assert sk.plan(kmaj, sk.Config(f32_kernel="tf32x3"), num_sms=152).tile_k == 32
+    for kw in ({"b_layout": "row"}, {"a_layout": "col"}):
+        p = sk.shape_problem(384, 384, 2048, dtype="f32", **kw)
+        assert sk.plan(p, num_sms=152).tile_k == 16
+        with pytest.raises(sk.SkError):
+            sk.plan(p, sk.Config(f32_kernel="tf32x3"), num_sms=152)
+    assert _q(sk, kmaj, {"f32_kernel": 3})[0] == B.SK_ERR_INVALID_ARG
+    # the 3xTF32 tile is 128 x 128 on single CTAs
+    with pytest.raises(sk.SkError):
+        sk.plan(kmaj, sk.Config(f32_kernel="tf32x3", tile_m=256), num_sms=152)
+
+
 def test_tile_aligned_unit_count(sk):
     """With fewer tiles than units and the count left to the library, the
     runtime model may cut every tile into equal parts: k x T units, each

@@ -1,4 +1,5 @@
-"""GPU parity of the FP32 SIMT Stream-K path against the FP64 oracle."""
+"""GPU parity of the FP32 Stream-K paths against the FP64 oracle: the FFMA
+(SIMT) kernel and the 3xTF32 tensor-core kernel."""
 import numpy as np
 import pytest
 import torch
@@ -10,6 +11,7 @@ from gpu_common import assert_within_bound, dev, same_strides, sk, to_np
 pytestmark = pytest.mark.gpu
 
 MODES = ["dp", "sk", "hybrid1", "hybrid2"]
+KERNELS = ["ffma", "tf32x3"]
 
 
 @pytest.fixture(scope="module")
@@ -25,24 +27,29 @@ def _run(m, a, b, **kw):
     return c
 
 
+@pytest.mark.parametrize("kern", KERNELS)
 @pytest.mark.parametrize("mode", MODES)
-def test_fp32_config1_modes(m, mode):
+def test_fp32_config1_modes(m, mode, kern):
     """384x384x2048, 128x128 tiles: 9 tiles < SMs, so SK splits every tile."""
     cfg = workloads.FP32_SMALL
     a, b = workloads.gemm_inputs(cfg["M"], cfg["N"], cfg["K"], dtype="f32", seed=0)
-    c = _run(m, a, b, config=m.Config(mode=mode))
-    assert_within_bound(c, a, b, what=f"fp32 {mode}")
+    c = _run(m, a, b, config=m.Config(mode=mode, f32_kernel=kern))
+    assert_within_bound(c, a, b, what=f"fp32 {mode} {kern}")
 
 
-def test_fp32_small_int_exact(m):
+@pytest.mark.parametrize("kern", KERNELS)
+def test_fp32_small_int_exact(m, kern):
+    """Small integers are exact in TF32 too (low parts zero), and every
+    partial sum is an integer below 2^24: both kernels give the exact C."""
     a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=1, dist="int")
     ref, _ = oracle.gemm(a, b)
     for mode in MODES:
-        c = _run(m, a, b, config=m.Config(mode=mode))
+        c = _run(m, a, b, config=m.Config(mode=mode, f32_kernel=kern))
         assert np.array_equal(to_np(c), ref), mode
 
 
-def test_fp32_unit_count_sweep(m):
+@pytest.mark.parametrize("kern", KERNELS)
+def test_fp32_unit_count_sweep(m, kern):
     """Every CTA count g, including the sub-maximal ones the paper's
     Methodology/Results report as broken in the studied implementation."""
     sms = torch.cuda.get_device_properties(dev()).multi_processor_count
@@ -50,39 +57,46 @@ def test_fp32_unit_count_sweep(m):
     ref, _ = oracle.gemm(a, b)
     for g in sorted({1, 2, 3, 7, sms // 2, sms - 1, sms}):
         for mode in ("sk", "hybrid2"):
-            c = _run(m, a, b, config=m.Config(mode=mode, num_ctas=g, min_iters_per_unit=1))
+            c = _run(m, a, b, config=m.Config(mode=mode, num_ctas=g, min_iters_per_unit=1, f32_kernel=kern))
             assert np.array_equal(to_np(c), ref), (g, mode)
 
 
 @pytest.mark.parametrize("al", ["row", "col"])
 @pytest.mark.parametrize("bl", ["row", "col"])
 @pytest.mark.parametrize("cl", ["row", "col"])
-def test_fp32_layouts_beta(m, al, bl, cl):
+@pytest.mark.parametrize("kern", ["auto", "ffma"])
+def test_fp32_layouts_beta(m, al, bl, cl, kern):
+    """auto: 3xTF32 for A row-major / B column-major, FFMA otherwise."""
     M, N, K = 130, 67, 93
     a, b = workloads.gemm_inputs(M, N, K, dtype="f32", a_layout=al, b_layout=bl, seed=3)
     c0 = workloads.as_layout(workloads.uniform((M, N), seed=4), cl)
     d = dev()
     ad, bd, c0d = same_strides(a, d), same_strides(b, d), same_strides(c0, d)
     out = torch.empty_strided(c0.shape, c0.stride(), device=d)
-    m.gemm(ad, bd, out, alpha=0.75, beta=-1.5, C_in=c0d, config=m.Config(mode="sk"))
+    m.gemm(ad, bd, out, alpha=0.75, beta=-1.5, C_in=c0d, config=m.Config(mode="sk", f32_kernel=kern))
     assert m.default_workspace(d).status() == 0
     assert_within_bound(out, a, b, alpha=0.75, beta=-1.5, C0=c0, what=f"{al}{bl}{cl}")
 
 
-@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 127, 129), (129, 257, 33), (480, 512, 512), (5, 300, 4000)])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 127, 129), (129, 257, 33), (480, 512, 512), (5, 300, 4000),
+                                   (131, 260, 36), (300, 129, 1028)])
 def test_fp32_ragged(m, shape):
+    """Ragged tiles and K; K a multiple of 4 runs 3xTF32 (TMA), others FFMA."""
     M, N, K = shape
     a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=5)
-    for mode in ("sk", "dp"):
-        c = _run(m, a, b, config=m.Config(mode=mode, min_iters_per_unit=1))
-        assert_within_bound(c, a, b, what=f"{shape} {mode}")
+    kerns = ("auto", "ffma", "tf32x3") if K % 4 == 0 else ("auto", "ffma")
+    for kern in kerns:
+        for mode in ("sk", "dp"):
+            c = _run(m, a, b, config=m.Config(mode=mode, min_iters_per_unit=1, f32_kernel=kern))
+            assert_within_bound(c, a, b, what=f"{shape} {mode} {kern}")
 
 
-def test_fp32_deterministic_and_graph(m):
+@pytest.mark.parametrize("kern", KERNELS)
+def test_fp32_deterministic_and_graph(m, kern):
     a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=6)
     d = dev()
     ad, bd = a.to(d), b.to(d)
-    cfg = m.Config(mode="sk")
+    cfg = m.Config(mode="sk", f32_kernel=kern)
     c1 = m.gemm(ad, bd, config=cfg)
     c2 = m.gemm(ad, bd, config=cfg)
     assert torch.equal(c1, c2)
@@ -112,7 +126,8 @@ def test_fp32_k_zero(m):
     assert torch.equal(out, torch.zeros_like(out))
 
 
-def test_fp32_timeout_status_and_recovery(m):
+@pytest.mark.parametrize("kern", KERNELS)
+def test_fp32_timeout_status_and_recovery(m, kern):
     """Peers withhold their flags (test-only injection): every owner's
     bounded wait must expire, the kernel must return, the status word must
     read SK_ERR_TIMEOUT, and the context must stay usable."""
@@ -123,10 +138,50 @@ def test_fp32_timeout_status_and_recovery(m):
     sms = torch.cuda.get_device_properties(d).multi_processor_count
     # owner protocol (count fixed: the library picks no other protocol), then
     # the split reduce, whose peers then withhold their arrival
-    for cfg in (dict(num_ctas=sms), dict(num_ctas=144, fixup="split")):
+    for cfg in (dict(num_ctas=sms, f32_kernel=kern), dict(num_ctas=144, fixup="split", f32_kernel=kern)):
         m.gemm(ad, bd, config=m.Config(mode="sk", timeout_ns=50_000_000, debug_flags=1, **cfg), workspace=ws)
         assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT, cfg
         m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
         c = m.gemm(ad, bd, config=m.Config(mode="sk", **cfg), workspace=ws)
         assert ws.status() == 0
         assert_within_bound(c, a, b, what=f"after timeout {cfg}")
+
+
+def test_tf32x3_accuracy_and_fixups(m):
+    """3xTF32 on long K stays inside the FP32 bound with a wide margin
+    (dropped a_lo b_lo and low-part rounding: ~2^-21 |a b| per product), and
+    its three fixup protocols give identical bits."""
+    d = dev()
+    M, N, K = 256, 384, 16384
+    a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=9)
+    ref, S = oracle.gemm(a, b)
+    ad, bd = a.to(d), b.to(d)
+    outs = {}
+    for fx in ("owner", "last_arriver", "split"):
+        # 6 tiles x 16 units: ranges of 32 of the 512 k-blocks (split-eligible)
+        cfg = m.Config(mode="sk", num_ctas=96, fixup=fx, f32_kernel="tf32x3")
+        outs[fx] = m.gemm(ad, bd, config=cfg)
+        assert m.default_workspace(d).status() == 0
+    assert torch.equal(outs["owner"], outs["last_arriver"]) and torch.equal(outs["owner"], outs["split"])
+    assert_within_bound(outs["owner"], a, b, what="tf32x3 K=16384")
+    # The worst error relative to S sits at the scale of the products'
+    # error, 2^-21 (measured 3.1e-7; the FFMA kernel 3.0e-8), far inside
+    # the 5e-5 bound.
+    rel = float((np.abs(to_np(outs["owner"]).astype(np.float64) - ref) / S).max())
+    assert rel < 2.0 ** -20, rel
+
+
+def test_tf32x3_grouped(m):
+    """Grouped FP32 problems in one 3xTF32 launch."""
+    d = dev()
+    shapes = [(256, 128, 512), (100, 300, 64), (384, 384, 2048), (1, 8, 4)]
+    As, Bs, refs = [], [], []
+    for i, (M, N, K) in enumerate(shapes):
+        a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=40 + i, dist="int")
+        As.append(a.to(d))
+        Bs.append(same_strides(b, d))
+        refs.append(oracle.gemm(a, b)[0])
+    outs = m.grouped_gemm(As, Bs, config=m.Config(mode="sk", f32_kernel="tf32x3"))
+    assert m.default_workspace(d).status() == 0
+    for o, r, sh in zip(outs, refs, shapes):
+        assert np.array_equal(to_np(o), r), sh
