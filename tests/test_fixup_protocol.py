@@ -197,3 +197,34 @@ def _split_explore(kc, empty):
 @pytest.mark.parametrize("kc,empty", [(2, ()), (3, ()), (3, (1,)), (4, (0, 2)), (3, (0, 1))])
 def test_split_reduce_every_interleaving(kc, empty):
     assert _split_explore(kc, empty) > 0
+
+
+@pytest.mark.parametrize("bn,f32_out", [(128, True), (128, False), (256, True), (256, False)])
+@pytest.mark.parametrize("kc", [2, 3, 4, 5, 8, 9, 16, 17, 32, 64])
+def test_split_units_cover_the_tile_once(bn, f32_out, kc):
+    """The tensor-core split reduce deals (column group x warp) units to the
+    contributors: unit s is chunk group s // 4 of warp s % 4, contributor j
+    takes [j*NS/kc, (j+1)*NS/kc).  Every (chunk, warp) block of the tile is
+    summed by exactly one warp of one contributor, and a warp's units are
+    what that warp keeps in TMEM (not spilled)."""
+    uw = 1 if f32_out else 2                 # chunks per unit: 32 or 64 columns
+    nch = bn // 32
+    ns = 4 * nch // uw
+    owner = {}
+    for j in range(kc):
+        s0, s1 = j * ns // kc, (j + 1) * ns // kc
+        for q4 in range(4):
+            s_first = s0 + ((q4 - s0 % 4) + 4) % 4
+            n_w = (s1 - 1 - s_first) // 4 + 1 if s_first < s1 else 0
+            # the warp's chunks, in the order the kernel walks them
+            chunks = [((s_first + 4 * (k // uw)) // 4) * uw + k % uw for k in range(n_w * uw)]
+            kept = [ch for ch in range(nch) if s0 <= (ch // uw) * 4 + q4 < s1]
+            assert sorted(chunks) == kept
+            for ch in chunks:
+                assert (ch, q4) not in owner
+                owner[(ch, q4)] = j
+    assert set(owner) == {(ch, q4) for ch in range(nch) for q4 in range(4)}
+    # BF16 output: a warp always holds both chunks of a 64-column TMA box
+    if not f32_out:
+        for (ch, q4), j in owner.items():
+            assert owner[(ch ^ 1, q4)] == j
