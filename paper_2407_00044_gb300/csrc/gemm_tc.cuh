@@ -616,15 +616,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           for (int g0 = 0; g0 < nunits; g0 += nb, ++group) {
             const int gn = nunits - g0 < nb ? nunits - g0 : nb;
             if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
-            if (et == 0) {
-              fence_proxy_async_all();   // the acquired partials, to the copy engine
-              for (int b = 0; b < gn; ++b) {
-                const int i = g0 + b;
-                const int ch = i / nst;
-                const uint32_t fb = smem_u32(fix_bar + b);
-                mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
-                bulk_copy_g2s(tiles_addr + b * FIX_UNIT_BYTES, src_of(ch, i - ch * nst), FIX_UNIT_BYTES, fb);
-              }
+            if (et < gn) {
+              // one copy per thread (gn <= FIX_SMEM_UNITS): address
+              // arithmetic and issue in parallel
+              const int i = g0 + et;
+              const int ch = i / nst;
+              const uint32_t fb = smem_u32(fix_bar + et);
+              fence_proxy_async_global();   // the acquired partials, to the copy engine
+              mbar_arrive_expect_tx(fb, FIX_UNIT_BYTES);
+              bulk_copy_g2s(tiles_addr + et * FIX_UNIT_BYTES, src_of(ch, i - ch * nst), FIX_UNIT_BYTES, fb);
             }
             for (int b = 0; b < gn; ++b) {
               const int i = g0 + b;
@@ -817,26 +817,33 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             };
             const int npieces = nunit_w * UW * nst;
             if (ring_free) {
-              // Stage the pieces in this warp's quarter of the idle operand
-              // ring with 4 KB bulk copies, a group at a time on one barrier.
+              // Stage the pieces in this warp's share of the idle operand
+              // ring (the ring split among the CTA's summing warps) with 4 KB
+              // bulk copies, a group at a time on one barrier.
               constexpr int PIECE = 4096;
-              int nb = (stages * STAGE_BYTES / 4) / PIECE;
-              const uint32_t wbase = tiles_addr + (uint32_t)(q4 * (stages * STAGE_BYTES / 4));
-              const float4 *wsmem = reinterpret_cast<const float4 *>(smem + q4 * (stages * STAGE_BYTES / 4));
+              const int nw = s1 - s0 < 4 ? s1 - s0 : 4;       // warps of this CTA that sum
+              const int wq = (q4 - s0 % 4 + 4) % 4;            // this warp's place among them
+              const int region = (stages * STAGE_BYTES / nw) / PIECE * PIECE;
+              int nb = region / PIECE;
+              if (nb > 32) nb = 32;                            // one copy per lane
+              const uint32_t wbase = tiles_addr + (uint32_t)(wq * region);
+              const float4 *wsmem = reinterpret_cast<const float4 *>(smem + wq * region);
               const uint32_t fb = smem_u32(fix_bar + q4);
               float v[32];
               int group = 0;
               bool okw = true;
+              int kq = 0, ti = 0;   // chunk (of this warp's) and term of the next piece
               for (int g0 = 0; g0 < npieces && okw; g0 += nb, ++group) {
                 const int gn = npieces - g0 < nb ? npieces - g0 : nb;
                 __syncwarp();   // the previous group's images are consumed
-                if (lane == 0) {
-                  fence_proxy_async_all();   // the acquired partials, to the copy engine
-                  mbar_arrive_expect_tx(fb, (uint32_t)(gn * PIECE));
-                  for (int bi = 0; bi < gn; ++bi) {
-                    const int i = g0 + bi;
-                    bulk_copy_g2s(wbase + bi * PIECE, block_of(chunk_of(i / nst), i % nst), PIECE, fb);
-                  }
+                if (lane == 0) mbar_arrive_expect_tx(fb, (uint32_t)(gn * PIECE));
+                __syncwarp();
+                if (lane < gn) {
+                  // one copy per lane (gn <= 32): the address arithmetic and
+                  // the issue run in parallel
+                  const int i = g0 + lane;
+                  fence_proxy_async_global();   // the acquired partials, to the copy engine
+                  bulk_copy_g2s(wbase + lane * PIECE, block_of(chunk_of(i / nst), i % nst), PIECE, fb);
                 }
                 if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE, 11, nitem, globaltimer_ordered());
                 if (!__all_sync(0xffffffffu, mbar_wait(fb, (uint32_t)(group & 1), tmo))) {
@@ -846,13 +853,16 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                 }
                 if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
                 for (int bi = 0; bi < gn; ++bi) {
-                  const int i = g0 + bi;
-                  const int ch = chunk_of(i / nst), ti = i % nst;
+                  const int ch = chunk_of(kq);
                   if (ti == jx) add_own(ch, v);   // own term comes before this one
                   add_block(wsmem + bi * (PIECE / 16), ti == 0 && jx != 0, false, v);
                   if (ti == nst - 1) {
                     if (jx == kc - 1) add_own(ch, v);   // own term is the last
                     store_chunk(ch, v, alpha);
+                    ti = 0;
+                    ++kq;
+                  } else {
+                    ++ti;
                   }
                 }
               }

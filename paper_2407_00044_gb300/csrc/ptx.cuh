@@ -91,6 +91,9 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uin
 // Orders this thread's generic-proxy view of memory before its later
 // async-proxy (TMA / bulk copy) accesses.
 __device__ __forceinline__ void fence_proxy_async_all() { asm volatile("fence.proxy.async;" ::: "memory"); }
+// Same, restricted to the global state space (generic global accesses vs
+// async-proxy ones; measured cheaper than the unrestricted fence).
+__device__ __forceinline__ void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 // TMA tensor store shared -> global (bulk-group completion).
 __device__ __forceinline__ void tma_store_2d(const void *tmap, uint32_t src, int32_t x, int32_t y) {
