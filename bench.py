@@ -491,6 +491,8 @@ def run_workload(args, world, rank, local):
                      f"FFMA row: {sms} SMs x 128 lanes x 2 flop x 2.07 GHz (derived)")
         ffma_peak = sms * 128 * 2 * 2.07e9 / 1e12
         M, N, K = (workloads.FP32_SMALL[x] for x in ("M", "N", "K"))
+        if args.only:
+            M, N, K = (int(x) for x in args.only.split(","))
         A = workloads.device_uniform((M, K), seed=5000, device=dev, dtype=torch.float32)
         Bm = workloads.device_uniform((N, K), seed=5001, device=dev, dtype=torch.float32).t()
         C = torch.empty(M, N, dtype=torch.float32, device=dev)
@@ -504,8 +506,8 @@ def run_workload(args, world, rank, local):
         t = _timed_region(lambda: sk.gemm(A, Bm, C, config=ff), steps, flush)
         tdp = _timed_region(lambda: sk.gemm(A, Bm, C, config=ffdp), steps, flush)
         rows.append((f"ffma kernel {M}x{N}x{K} f32", workloads.gemm_flops(M, N, K), t, tdp, ffma_peak))
-        desc = (f"FP32 {M}x{N}x{K}, A row-major, B column-major, uniform[-1,1]; 128x128 tiles "
-                "(9 tiles, fewer than SMs: every tile is split), 3xTF32 tensor-core kernel (FFMA kernel as context)")
+        desc = (f"FP32 {M}x{N}x{K}, A row-major, B column-major, uniform[-1,1]; 128x128 tiles, "
+                "3xTF32 tensor-core kernel (FFMA kernel as context)")
     else:
         raise ValueError(args.workload)
     if ws_status(sk, dev) != 0:
@@ -656,7 +658,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-step-seconds", type=float, default=3.0)
-    ap.add_argument("--only", default="", help="M,N,K: time this one problem instead of the sweep")
+    ap.add_argument("--only", default="", help="M,N,K: time this one problem instead of the sweep "
+                    "(with --workload f32: instead of 384,384,2048)")
     ap.add_argument("--mode", default="auto", choices=["auto", "dp", "sk", "hybrid1", "hybrid2"])
     ap.add_argument("--no-dp", dest="dp", action="store_false", help="skip the data-parallel baseline")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer run")
