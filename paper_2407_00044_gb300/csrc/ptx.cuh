@@ -165,8 +165,8 @@ __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_
       : "memory");
 }
 
-// Same for kind::tf32 (FP32 bit patterns read as TF32: the low 13
-// mantissa bits are ignored).
+// Same for kind::tf32 (operands are TF32 values in 32-bit containers; the
+// callers pass values already rounded to TF32, low 13 mantissa bits zero).
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
