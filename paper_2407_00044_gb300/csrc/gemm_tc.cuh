@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   constexpr int B_ROWS = PAIR ? BN / 2 : BN;    // rows of B (N direction) this CTA loads
   constexpr int A_BYTES = 128 * 128;
   constexpr int B_BYTES = B_ROWS * 128;
-  // 3xTF32: each stage holds the loaded operands (converted in place to
+  // 3xTF32: each stage holds the loaded operands (read by the MMA as
   // their TF32 high parts) followed by their low parts.
   constexpr bool X3 = IN == IN_TF32X3;
   constexpr int OP_BYTES = A_BYTES + B_BYTES;
@@ -474,11 +474,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     while (cursor_next(S, P.ps, u, c, w)) {
       const TcProblem &pr = P.prob[w.problem];
       if constexpr (X3) {
-        // Split every loaded FP32 value x of the item's stages into
-        // x_hi = tf32(x), written over x, and x_lo = tf32(x - x_hi), written
-        // OP_BYTES further on (x - x_hi is exact in FP32); then hand the
-        // stage to the MMA issuer.  The operation is elementwise, so the
-        // swizzled layout is kept as TMA wrote it.
+        // Split every loaded FP32 value x of the item's stages: the MMA
+        // reads the FP32 container itself as x_hi (kind::tf32 drops the low
+        // 13 mantissa bits: x_hi = x truncated to TF32), and x_lo =
+        // tf32_rn(x - x_hi) (the difference is exact in FP32) is written
+        // OP_BYTES further on; then the stage goes to the MMA issuer.  The
+        // operation is elementwise, so the swizzled layout is kept as TMA
+        // wrote it.  (Measured: with x_lo taken against truncation the
+        // worst error is 3.3e-7 of S at K = 16384; had the MMA rounded the
+        // container instead, it would be of order 2^-11.)
         for (int kb = w.k0; kb < w.k1; ++kb) {
           if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(full_bar + cstage), cphase, tmo)) || *abort_flag) {
             if (lane == 0) fail();
@@ -489,8 +493,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 #pragma unroll 4
           for (int i = et; i < OP_BYTES / 16; i += 128) {
             const float4 v = x[i];
-            const float4 h = make_float4(round_tf32(v.x), round_tf32(v.y), round_tf32(v.z), round_tf32(v.w));
-            x[i] = h;
+            const float4 h = make_float4(trunc_tf32(v.x), trunc_tf32(v.y), trunc_tf32(v.z), trunc_tf32(v.w));
             lo[i] = make_float4(round_tf32(v.x - h.x), round_tf32(v.y - h.y), round_tf32(v.z - h.z),
                                 round_tf32(v.w - h.w));
           }

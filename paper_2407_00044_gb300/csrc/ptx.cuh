@@ -165,8 +165,8 @@ __device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_
       : "memory");
 }
 
-// Same for kind::tf32 (operands are TF32 values in 32-bit containers; the
-// callers pass values already rounded to TF32, low 13 mantissa bits zero).
+// Same for kind::tf32 (TF32 operands in 32-bit containers: an FP32 value
+// is read with its low 13 mantissa bits dropped, i.e. truncated to TF32).
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
@@ -176,6 +176,10 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+
+// x truncated to TF32: the low 13 mantissa bits cleared (what kind::tf32
+// MMAs read from an FP32 container).
+__device__ __forceinline__ float trunc_tf32(float x) { return __uint_as_float(__float_as_uint(x) & 0xffffe000u); }
 
 // x rounded to TF32 (10 explicit mantissa bits, nearest, ties away from
 // zero), as an FP32 value with the low 13 bits clear.
