@@ -49,6 +49,28 @@ def test_static_ws_matches_sk_gemm_two_calls():
         assert np.all(np.abs(got - ref) <= tol), f"call {call}"
 
 
+@pytest.mark.parametrize("f32k", ["tf32x3", "ffma"])
+def test_static_ws_fp32_bitwise(f32k):
+    """FP32 (both kernels) through the fixed workspace: the same schedule
+    and summation order as with a caller workspace, so the same bits."""
+    m = sk()
+    B = m.binding
+    d = dev()
+    ws = m.Workspace(d)
+    cfg = m.Config(mode="sk", f32_kernel=f32k).to_c()
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=320)
+    ad, bd = a.to(d), b.to(d)
+    c_ref = torch.empty(384, 384, device=d)
+    c_new = torch.full((384, 384), float("nan"), device=d)
+    B.check(B.sk_gemm(ctypes.byref(m.make_problem(ad, bd, c_ref)), ctypes.byref(cfg), ws.ptr, ws.nbytes,
+                      _stream()), "sk_gemm")
+    B.check(B.sk_gemm_static_ws(ctypes.byref(m.make_problem(ad, bd, c_new)), ctypes.byref(cfg), _stream()),
+            "sk_gemm_static_ws")
+    torch.cuda.synchronize()
+    assert ws.status() == 0
+    assert torch.equal(c_new, c_ref)
+
+
 def test_static_ws_rejects_oversized_plan():
     m = sk()
     B = m.binding
