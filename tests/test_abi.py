@@ -276,6 +276,17 @@ def test_library_split_choice_is_eligible(sk, shape):
         assert len(sk.unit_items(p, u, cfg, num_sms=152)) == 1
 
 
+def test_fault_injection_keeps_the_owner_protocol(sk):
+    """With the test-only injection set (peers withhold their flags), the
+    library never picks the split reduce by itself, and the decision cache
+    keeps the two requests apart."""
+    B = sk.binding
+    p = sk.shape_problem(384, 384, 2048, dtype="f32")
+    assert sk.plan(p, num_sms=152).fixup == B.SK_FIXUP_SPLIT
+    assert sk.plan(p, sk.Config(debug_flags=1), num_sms=152).fixup == B.SK_FIXUP_OWNER
+    assert sk.plan(p, num_sms=152).fixup == B.SK_FIXUP_SPLIT
+
+
 def test_f32_kernel_choice(sk):
     """FP32 problems go to the 3xTF32 tensor-core kernel (32-deep k-blocks)
     when both operands are K-major and TMA-aligned, else to the FFMA
