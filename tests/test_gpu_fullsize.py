@@ -93,3 +93,17 @@ def test_autograd_full_size_sampled(m):
     assert_sampled(A.grad, G, Bm.detach().t(), out="bf16", n_rand=24, what="dA")
     assert_sampled(Bm.grad, A.detach().t(), G, out="bf16", n_rand=24, what="dB")
     assert A.grad.stride() == A.stride() and Bm.grad.stride() == Bm.stride()
+
+
+@pytest.mark.parametrize("f32k", ["tf32x3", "ffma"])
+def test_fp32_4096_cube_sampled(m, f32k):
+    """FP32 4096^3 in the library's default launch configuration for each
+    FP32 kernel (3xTF32: 128x128 tiles, hybrid Stream-K over 1024 tiles),
+    sampled rows/columns against the FP64 oracle within the FP32 bound."""
+    d = dev()
+    M = N = K = 4096
+    A = workloads.device_uniform((M, K), seed=61, device=d, dtype=torch.float32)
+    Bm = workloads.device_uniform((N, K), seed=62, device=d, dtype=torch.float32).t()
+    C = m.gemm(A, Bm, config=m.Config(f32_kernel=f32k))
+    assert m.default_workspace(d).status() == 0
+    assert_sampled(C, A, Bm, out="f32", tile_m=128, tile_n=128, n_rand=32, what=f"fp32 4096^3 {f32k}")
