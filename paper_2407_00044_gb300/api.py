@@ -156,14 +156,19 @@ _ws_cache: dict = {}
 
 
 def default_workspace(device=None) -> Workspace:
+    """The workspace calls without an explicit one use: one per device and
+    stream (the current stream of that device), so GEMMs running on
+    different streams at the same time never share partial slots or flags.
+    Calls on one stream are ordered by it and share its workspace."""
     dev = torch.device(device if device is not None else torch.cuda.current_device())
     if dev.index is None:
         dev = torch.device("cuda", torch.cuda.current_device())
+    key = (dev.index, torch.cuda.current_stream(dev).cuda_stream)
     with _ws_lock:
-        ws = _ws_cache.get(dev.index)
+        ws = _ws_cache.get(key)
         if ws is None:
             ws = Workspace(dev)
-            _ws_cache[dev.index] = ws
+            _ws_cache[key] = ws
         return ws
 
 

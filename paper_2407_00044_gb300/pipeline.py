@@ -22,7 +22,9 @@ class HostGemmPipeline:
         the copies run asynchronously."""
         self.device = torch.device(device if device is not None else torch.cuda.current_device())
         self.config = config
-        self.ws = workspace or api.default_workspace(self.device)
+        # its own workspace unless given one: its GEMMs run on a stream of
+        # their own
+        self.ws = workspace or api.Workspace(self.device)
         self.host = list(problems)
         self.dev = []
         for (a, b, c) in self.host:

@@ -106,3 +106,27 @@ def test_bf16_output_beyond_int32_elements(m, beta):
         assert torch.allclose(got, want, rtol=2 ** -7, atol=2e-2)
     del C, C_in
     torch.cuda.empty_cache()
+
+
+def test_default_workspace_per_stream(m):
+    """Calls without a workspace on different streams use different
+    workspaces, so concurrent GEMMs never share partial slots or flags;
+    both give the oracle's exact result."""
+    d = dev()
+    a, b = workloads.gemm_inputs(600, 520, 4096, dtype="bf16", seed=130, dist="int")
+    ref, _ = oracle.gemm(a, b)
+    ad, bd = same_strides(a, d), same_strides(b, d)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = []
+    cfg = m.Config(mode="sk")
+    wss = []
+    for s in (s1, s2):
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            wss.append(m.default_workspace(d))
+            outs.append(m.gemm(ad, bd, out_dtype=torch.float32, config=cfg))
+    assert wss[0] is not wss[1]
+    torch.cuda.synchronize()
+    for s, ws, c in zip((s1, s2), wss, outs):
+        assert ws.status() == 0
+        assert np.array_equal(to_np(c), ref)
