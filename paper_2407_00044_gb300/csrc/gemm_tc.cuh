@@ -580,15 +580,30 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       // rows is one 16 KB block and a warp's 32 rows of it one 4 KB block.
       // Leaves out the chunks for which skip(ch) holds.
       auto spill = [&](float4 *slot, auto skip) {
+        // two chunks per TMEM load where both leave
 #pragma unroll 1
-        for (int ch = 0; ch < BN / 32; ++ch) {
-          if (skip(ch)) continue;
-          float v[32];
-          tmem_ld32(tbase + ch * 32, v);
+        for (int ch = 0; ch < BN / 32; ch += 2) {
+          const bool s0 = skip(ch), s1 = skip(ch + 1);
+          if (s0 && s1) continue;
+          if (!s0 && !s1) {
+            float v[64];
+            tmem_ld64(tbase + ch * 32, v);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            __stcg(slot + ((ch * 4 + q4) * 8 + j) * 32 + lane,
-                   make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                __stcg(slot + (((ch + h) * 4 + q4) * 8 + j) * 32 + lane,
+                       make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2],
+                                   v[32 * h + 4 * j + 3]));
+          } else {
+            const int c1 = s0 ? ch + 1 : ch;
+            float v[32];
+            tmem_ld32(tbase + c1 * 32, v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              __stcg(slot + ((c1 * 4 + q4) * 8 + j) * 32 + lane,
+                     make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+          }
         }
       };
       auto no_skip = [](int) { return false; };
@@ -954,10 +969,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       } else {
         const float alpha = get_alpha();
 #pragma unroll 1
-        for (int ch = 0; ch < BN / 32; ++ch) {
-          float v[32];
-          tmem_ld32(tbase + ch * 32, v);
-          store_chunk(ch, v, alpha);
+        for (int ch = 0; ch < BN / 32; ch += 2) {
+          float v[64];
+          tmem_ld64(tbase + ch * 32, v);
+          store_chunk(ch, *reinterpret_cast<const float(*)[32]>(v), alpha);
+          store_chunk(ch + 1, *reinterpret_cast<const float(*)[32]>(v + 32), alpha);
         }
       }
       if (do_sum) {
