@@ -393,3 +393,41 @@ def test_layout_of_vector_operands(sk):
     p = sk.make_problem(a, b, c)
     assert (p.b_layout, p.ldb) == (B.SK_COL_MAJOR, 64)
     assert sk.plan(p, sk.Config(tile_m=128, tile_n=128), num_sms=152).tiles == 3
+
+
+def test_library_split_choice_on_random_problem_sets(sk):
+    """Random single and grouped problem sets: whenever the library picks
+    the split reduce by itself, the plan it returns has every unit holding
+    exactly one range (the kernels' precondition), the unit count is a
+    multiple of the tile count, and the ranges cover every tile once."""
+    import random
+    B = sk.binding
+    rng = random.Random(7)
+    picked = 0
+    for _ in range(60):
+        n = rng.choice([1, 1, 1, 2, 3])
+        shapes = [(rng.choice([128, 256, 384, 512, 768, 1024]), rng.choice([128, 256, 384, 512, 768]),
+                   rng.choice([1024, 2048, 4096, 8192, 16384])) for _ in range(n)]
+        dtype = rng.choice(["bf16", "bf16", "f32"])
+        probs = [sk.shape_problem(*s, dtype=dtype) for s in shapes]
+        info = sk.plan(probs, num_sms=152)
+        if info.fixup != B.SK_FIXUP_SPLIT:
+            continue
+        picked += 1
+        units = info.num_ctas
+        assert units % info.tiles == 0 and info.extra_units == 0
+        cfg = sk.Config(mode="sk", tile_m=info.tile_m, tile_n=info.tile_n,
+                        num_ctas=2 * units if info.tile_m == 256 else units, fixup="split")
+        seen = {}
+        for u in range(units):
+            its = sk.unit_items(probs, u, cfg, num_sms=152)
+            assert len(its) == 1, (shapes, u)
+            it = its[0]
+            seen.setdefault((it.problem, it.tile), []).append((it.k0, it.k1))
+        assert len(seen) == info.tiles
+        for (p, t), ranges in seen.items():
+            ranges.sort()
+            assert ranges[0][0] == 0
+            assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+            assert ranges[-1][1] == -(-shapes[p][2] // info.tile_k)
+    assert picked > 0
