@@ -260,3 +260,36 @@ def test_workspace_shared_across_unit_counts(m):
             assert np.array_equal(to_np(c), ref), fix
             assert _flags_zero(m, 152)
     assert m.default_workspace(d).status() == 0
+
+
+def test_library_split_random_shapes(m):
+    """Random shapes where the library picks the split reduce by itself:
+    the result equals, bit for bit, the same plan with the owner protocol
+    (integer inputs: both are also the oracle's exact result)."""
+    import random
+    d = dev()
+    rng = random.Random(11)
+    sms = torch.cuda.get_device_properties(d).multi_processor_count
+    done = 0
+    for _ in range(40):
+        if done >= 8:
+            break
+        M = rng.choice([128, 200, 256, 384, 520, 768])
+        N = rng.choice([128, 136, 256, 384, 512, 640])
+        K = rng.choice([1024, 2048, 4096, 8192])
+        dtype = rng.choice(["bf16", "f32"])
+        info = m.plan(m.shape_problem(M, N, K, dtype=dtype), num_sms=sms)
+        if info.fixup != m.binding.SK_FIXUP_SPLIT:
+            continue
+        a, b = workloads.gemm_inputs(M, N, K, dtype=dtype, seed=700 + done, dist="int")
+        ad, bd = same_strides(a, d), same_strides(b, d)
+        kw = {} if dtype == "f32" else {"out_dtype": torch.float32}
+        c_auto = m.gemm(ad, bd, **kw)
+        units = info.num_ctas
+        c_owner = m.gemm(ad, bd, config=m.Config(mode="sk", tile_m=info.tile_m, tile_n=info.tile_n,
+                                                 num_ctas=2 * units if info.tile_m == 256 else units), **kw)
+        assert m.default_workspace(d).status() == 0
+        assert torch.equal(c_auto, c_owner), (M, N, K, dtype)
+        assert np.array_equal(to_np(c_auto), oracle.gemm(a, b)[0]), (M, N, K, dtype)
+        done += 1
+    assert done > 0
