@@ -202,3 +202,43 @@ def test_paper_arithmetic_intensity():
     M, N, K = workloads.BF16_SWEEP[0]
     ai = workloads.gemm_flops(M, N, K) / workloads.gemm_bytes(M, N, K, 2, 2, 2)
     assert abs(ai - 1337) / 1337 < 2e-3
+
+
+def _tf32_trunc(x):
+    """x with its low 13 mantissa bits cleared (TF32 by truncation)."""
+    return (x.view(np.uint32) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def _tf32_rna(x):
+    """x rounded to TF32, nearest with ties away from zero: add half an
+    ulp of TF32 to the magnitude bits, then truncate."""
+    u = x.view(np.uint32)
+    return ((u + np.uint32(0x1000)) & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def test_3xtf32_split_meets_the_fp32_bound():
+    """The FP32 reading (3xTF32): with x_hi = x truncated to TF32 and
+    x_lo = tf32_rn(x - x_hi), a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
+    Emulated here in numpy (FP32 products of TF32 values are exact; the
+    sums run in FP32), the worst error against the FP64 oracle stays
+    below 2^-19 of S on mixed-sign and on one-signed inputs, two orders
+    under the 5e-5 bound.  One TF32 product alone (the FP32 container
+    read truncated, as the MMA reads it) errs by up to 2^-10 per product
+    in one direction, and on one-signed inputs the sum's error breaks the
+    bound."""
+    rng = np.random.default_rng(3)
+    M, N, K = 64, 48, 2048
+    for lo_v in (-1.0, 0.0):
+        a = rng.uniform(lo_v, 1, (M, K)).astype(np.float32)
+        b = rng.uniform(lo_v, 1, (K, N)).astype(np.float32)
+        ref, S = oracle.gemm(torch.from_numpy(a), torch.from_numpy(b))
+        a_hi, b_hi = _tf32_trunc(a), _tf32_trunc(b)
+        a_lo, b_lo = _tf32_rna(a - a_hi), _tf32_rna(b - b_hi)
+        assert np.all(np.abs(a - a_hi - a_lo) <= np.abs(a) * 2.0 ** -21)   # x_lo carries x - x_hi to 2^-21
+        c3 = a_hi @ b_hi + a_hi @ b_lo + a_lo @ b_hi                        # float32 throughout
+        rel3 = float((np.abs(c3.astype(np.float64) - ref) / S).max())
+        assert rel3 < 2.0 ** -19, (lo_v, rel3)
+        if lo_v == 0.0:
+            c1 = a_hi @ b_hi
+            rel1 = float((np.abs(c1.astype(np.float64) - ref) / S).max())
+            assert rel1 > 5e-5, rel1
