@@ -66,30 +66,63 @@ class TuneCache:
             os.replace(tmp, self.path)
 
 
+def _try(problem, cfg, num_sms):
+    try:
+        return api.plan(problem, cfg, num_sms=num_sms)
+    except B.SkError:
+        return None
+
+
+def _signature(info):
+    """What the kernel runs: modes that resolve to the same split of the
+    tiles give the same launch."""
+    return (info.tile_m, info.tile_n, info.tile_k, info.stages, info.num_ctas, info.sk_units,
+            info.sk_tiles, info.dp_tiles, info.iters_per_unit, info.extra_units, info.fixup)
+
+
 def candidates(problem: B.sk_problem, num_sms: int = 0):
-    """All valid configs with their predicted time, fastest first."""
+    """All valid configs with their predicted time, fastest first.  FP32
+    problems try both FP32 kernels; where every tile is split and there
+    are fewer tiles than units, the largest multiple of the tile count is
+    tried as well, with the owner fixup and with the split reduce."""
     out = []
+    seen = set()
+
+    def add(cfg, info):
+        sig = _signature(info)
+        if sig not in seen:
+            seen.add(sig)
+            out.append((cfg, float(info.predicted_us)))
+
+    f32_kernels = ["tf32x3", "ffma"] if problem.a_type == B.SK_F32 else ["auto"]
     for (tm, tn) in _TILES:
         for st in _STAGES[(tm, tn)]:
             for mode in _MODES:
-                cfg = api.Config(tile_m=tm, tile_n=tn, stages=st, mode=mode)
-                if problem.a_type == B.SK_F32:
-                    if (tm, tn) != (128, 128) or st != 6:
+                for fk in f32_kernels:
+                    cfg = api.Config(tile_m=tm, tile_n=tn, stages=st, mode=mode, f32_kernel=fk)
+                    if problem.a_type == B.SK_F32:
+                        if (tm, tn) != (128, 128) or st != 6:
+                            continue
+                        cfg = api.Config(tile_m=128, tile_n=128, mode=mode, f32_kernel=fk)
+                    info = _try(problem, cfg, num_sms)
+                    if info is None:
                         continue
-                    cfg = api.Config(tile_m=128, tile_n=128, mode=mode)
-                try:
-                    info = api.plan(problem, cfg, num_sms=num_sms)
-                except B.SkError:
-                    continue
-                out.append((cfg, float(info.predicted_us)))
-                # fewer tiles than units, all split: also the largest multiple
-                # of the tile count (every tile cut into equal parts)
-                T, g = info.tiles, info.num_ctas
-                if info.sk_tiles == T and 0 < T and 2 * T <= g and g // T * T != g:
-                    per = 2 if cfg.tile_m == 256 else 1
-                    cfg2 = api.Config(tile_m=cfg.tile_m, tile_n=cfg.tile_n, stages=cfg.stages, mode=cfg.mode,
-                                      num_ctas=per * (g // T * T))
-                    out.append((cfg2, float(api.plan(problem, cfg2, num_sms=num_sms).predicted_us)))
+                    add(cfg, info)
+                    # fewer tiles than units, all split: the largest multiple of
+                    # the tile count (every tile cut into equal parts), with
+                    # either fixup
+                    T, g = info.tiles, info.num_ctas
+                    if info.sk_tiles == T and 0 < T and 2 * T <= g:
+                        per = 2 if cfg.tile_m == 256 else 1
+                        for fx in ("owner", "split"):
+                            if fx == "owner" and g // T * T == g:
+                                continue   # the plan above
+                            cfg2 = api.Config(tile_m=cfg.tile_m, tile_n=cfg.tile_n, stages=cfg.stages,
+                                              mode=cfg.mode, num_ctas=per * (g // T * T), fixup=fx,
+                                              f32_kernel=fk)
+                            info2 = _try(problem, cfg2, num_sms)
+                            if info2 is not None:
+                                add(cfg2, info2)
     out.sort(key=lambda x: x[1])
     return out
 
