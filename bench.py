@@ -141,6 +141,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+SLOWDOWN_REASONS = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+
+
+def bad_clocks(c) -> bool:
+    """A clock record the timing rules reject: a hardware or thermal
+    slowdown reason, or an SM clock well below its maximum under load."""
+    if not c:
+        return False
+    return bool(SLOWDOWN_REASONS & set(c.get("reasons", []))) or c["sm_mhz"] < 0.8 * c["sm_max_mhz"]
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -232,15 +243,22 @@ def run_ours(args, world, rank, local):
         raise RuntimeError("device status after warm-up")
 
     # ---- timed region: Stream-K (default) arm
-    clocks = ClockSampler(local) if rank == 0 else None
-    barrier(world)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sk_ms = timed(auto, args.steps)
-    torch.cuda.synchronize()
-    barrier(world)
-    wall = time.perf_counter() - t0
-    clk = clocks.stop() if clocks else None
+    def timed_region():
+        clocks = ClockSampler(local) if rank == 0 else None
+        barrier(world)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ms = timed(auto, args.steps)
+        torch.cuda.synchronize()
+        barrier(world)
+        return ms, time.perf_counter() - t0, (clocks.stop() if clocks else None)
+
+    sk_ms, wall, clk = timed_region()
+    first_clocks = None
+    if world == 1 and bad_clocks(clk):
+        # a slowdown reason or a clock stuck low: measure once more
+        first_clocks = clk
+        sk_ms, wall, clk = timed_region()
     # ---- data-parallel baseline, same protocol
     dp_ms = timed(dp, args.steps) if args.dp else sk_ms
     if ws.status() != 0:
@@ -332,6 +350,9 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "wall_s_timed_region": round(wall, 3),
     }
+    if first_clocks is not None:
+        line["remeasured"] = {"first_clocks": first_clocks,
+                              "why": "slowdown reason or SM clock below 80 % of its maximum"}
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
     return line

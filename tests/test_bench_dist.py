@@ -51,3 +51,15 @@ def test_aggregate_two_ranks():
 def test_aggregate_single_rank():
     import bench
     assert bench.aggregate(5.0, 2.0, 1) == (5.0, 2.0)
+
+
+def test_clock_records_the_timing_rules_reject():
+    """bench.py measures once more when the clock record shows a hardware
+    or thermal slowdown or an SM clock stuck well below its maximum; a
+    power cap alone is kept."""
+    import bench
+    assert not bench.bad_clocks(None)
+    assert not bench.bad_clocks({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"]})
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.bad_clocks({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [r]})
+    assert bench.bad_clocks({"sm_mhz": 1200.0, "sm_max_mhz": 2070.0, "reasons": []})
