@@ -89,7 +89,7 @@ def profiled_traffic():
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling in the background (100 ms)."""
+    """nvidia-smi clock/throttle sampling in the background (every 20 ms)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -106,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={ident}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -242,25 +242,30 @@ def run_ours(args, world, rank, local):
     if ws.status() != 0:
         raise RuntimeError("device status after warm-up")
 
-    # ---- timed region: Stream-K (default) arm
-    def timed_region():
+    # ---- timed regions: the Stream-K (library default) arm, then the
+    # data-parallel arm, each with its own clock record; if either record
+    # shows a slowdown reason or a stuck clock, both arms are measured once
+    # more (the first records are kept in the line).
+    def timed_region(cfg):
         clocks = ClockSampler(local) if rank == 0 else None
         barrier(world)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ms = timed(auto, args.steps)
+        ms = timed(cfg, args.steps)
         torch.cuda.synchronize()
         barrier(world)
         return ms, time.perf_counter() - t0, (clocks.stop() if clocks else None)
 
-    sk_ms, wall, clk = timed_region()
+    def both_arms():
+        sk_r = timed_region(auto)
+        dp_r = timed_region(dp) if args.dp else sk_r
+        return sk_r, dp_r
+
+    (sk_ms, wall, clk), (dp_ms, dp_wall, dp_clk) = both_arms()
     first_clocks = None
-    if world == 1 and bad_clocks(clk):
-        # a slowdown reason or a clock stuck low: measure once more
-        first_clocks = clk
-        sk_ms, wall, clk = timed_region()
-    # ---- data-parallel baseline, same protocol
-    dp_ms = timed(dp, args.steps) if args.dp else sk_ms
+    if world == 1 and (bad_clocks(clk) or bad_clocks(dp_clk)):
+        first_clocks = {"sk": clk, "dp": dp_clk}
+        (sk_ms, wall, clk), (dp_ms, dp_wall, dp_clk) = both_arms()
     if ws.status() != 0:
         raise RuntimeError("device status after timing")
 
@@ -270,6 +275,10 @@ def run_ours(args, world, rank, local):
     total_flops, max_s = aggregate(total_flops_local, step_ms * args.steps / 1e3, world)
     value = total_flops / max_s / 1e12
 
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_mhz = clk["sm_mhz"] if clk else 2070.0
+    hw_at_clock = hw_dense_bf16(sms, clk_mhz)
+    hw_at_max = hw_dense_bf16(sms, clk["sm_max_mhz"] if clk else 2070.0)
     per_shape = []
     for (M, N, K), f, t_sk, t_dp, (a, b, c) in zip(shapes, flops, sk_ms, dp_ms, data):
         ms_sk = statistics.median(t_sk)
@@ -278,8 +287,10 @@ def run_ours(args, world, rank, local):
         per_shape.append({
             "M": M, "N": N, "K": K,
             "tile": f"{info.tile_m}x{info.tile_n}", "mode": ["auto", "dp", "sk", "hybrid1", "hybrid2"][info.mode],
+            "units": info.num_ctas, "fixup": ["owner", "last_arriver", "split"][info.fixup],
             "ms": round(ms_sk, 4), "tflops": round(f / ms_sk / 1e9, 1),
             "pct_peak": round(100 * f / ms_sk / 1e9 / pk["bf16"], 1),
+            "pct_hw": round(100 * f / ms_sk / 1e9 / hw_at_clock, 1),
             "dp_ms": round(ms_dp, 4), "dp_tflops": round(f / ms_dp / 1e9, 1),
             "sk_over_dp": round(ms_dp / ms_sk, 3),
         })
@@ -321,10 +332,27 @@ def run_ours(args, world, rank, local):
                 "kernel": "sk_tc_kernel<bf16,bf16,BN=256,pair> on %dx%dx%d" % shapes[di],
                 "peak_source": f"{pk['source']} bf16 burst (the launch is timed alone)",
                 # context: the same against the seconds-long sustained figure
-                "frac_of_sustained": round(achieved / pk["bf16_sustained"], 4)}
+                "frac_of_sustained": round(achieved / pk["bf16_sustained"], 4),
+                # and against the tensor cores' own dense rate at the sampled
+                # SM clock and at the maximum clock
+                "frac_of_hw_dense_at_sampled_clock": round(achieved / hw_at_clock, 4),
+                "frac_of_hw_dense_at_max_clock": round(achieved / hw_at_max, 4)}
 
     # ---- end-to-end through the public API with host buffers
     e2e = run_e2e(sk, shapes, data, args, ws, world) if args.e2e else None
+
+    # ---- the other configurations (FP32, FP8, grouped, autograd), each
+    # against its own data-parallel arm; not part of `value`
+    configs = None
+    if args.configs and not args.only:
+        del data
+        torch.cuda.empty_cache()
+        steps_cfg = max(5, min(args.steps, 20))
+        configs = {}
+        for name in ("f32", "fp8", "grouped", "autograd"):
+            configs[name] = workload_record(name, sk, dev, pk, steps_cfg, max(3, args.warmup),
+                                            lambda: l2_flush(0))
+            torch.cuda.empty_cache()
 
     if rank != 0:
         return None
@@ -338,7 +366,12 @@ def run_ours(args, world, rank, local):
                    "l2": "flushed before every GEMM by writing then reading a 256 MB buffer (outside the timed events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "dp_baseline": {"value": round(sum(flops) / (dp_step_ms / 1e3) / 1e12, 2), "unit": UNIT,
-                        "ms_per_step": round(dp_step_ms, 4)},
+                        "ms_per_step": round(dp_step_ms, 4), "clocks": dp_clk,
+                        "wall_s_timed_region": round(dp_wall, 3)},
+        "hw_dense_bf16": {"flop_per_clk_per_sm": SM_BF16_FLOP_PER_CLK, "sms": sms,
+                          "at_sampled_clock": round(hw_at_clock, 1), "at_max_clock": round(hw_at_max, 1),
+                          "unit": UNIT,
+                          "note": "pct_peak uses the measured cuBLAS burst; pct_hw this rate at the sampled clock"},
         "shapes": per_shape,
         "best_fixed_tile": None if not best_dp_ms else {
             "dp": {"value": round(sum(flops) / (sum(best_dp_ms) / 1e3) / 1e12, 2), "unit": UNIT},
@@ -350,8 +383,10 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
         "wall_s_timed_region": round(wall, 3),
     }
+    if configs is not None:
+        line["configs"] = configs
     if first_clocks is not None:
-        line["remeasured"] = {"first_clocks": first_clocks,
+        line["remeasured"] = {"first_clocks": first_clocks, "arms": "both arms measured again",
                               "why": "slowdown reason or SM clock below 80 % of its maximum"}
     if args.cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.cpu_seconds)
@@ -371,8 +406,9 @@ def run_e2e(sk, shapes, data, args, ws, world):
         host.append((ha, hbt.t(), hc))
     pipe = sk.HostGemmPipeline(host, device=data[0][0].device, workspace=ws)
     stream = torch.cuda.current_stream()
-    steps = max(1, min(args.steps, 5))
-    pipe.run()
+    steps = max(1, args.steps)
+    for _ in range(2):
+        pipe.run()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -406,24 +442,25 @@ def _timed_region(fn, steps, flush):
     return statistics.median(a.elapsed_time(b) for a, b in evs)
 
 
-def run_workload(args, world, rank, local):
-    """FP8, grouped, autograd and FP32 configurations, measured like the sweep
-    (inputs resident, L2 flushed, CUDA events), each next to its
-    data-parallel counterpart."""
-    import paper_2407_00044_gb300 as sk
-    dev = torch.device("cuda", torch.cuda.current_device())
-    pk = peaks()
-    flushbuf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    sink = torch.empty((), dtype=torch.float32, device=dev)
+SM_BF16_FLOP_PER_CLK = 8192   # dense BF16 tcgen05 rate of one SM (M128 N256 K16 per 128 cycles)
 
-    def flush():
-        flushbuf.fill_(1.0)
-        torch.sum(flushbuf, dim=0, out=sink)
 
-    steps = max(3, min(args.steps, 50))
+def hw_dense_bf16(sms: int, mhz: float) -> float:
+    """Dense BF16 tensor rate in TFLOP/s of `sms` SMs at `mhz`: SMs x 8192
+    flop per clock (one 128 x 256 x 16 MMA every 128 cycles per SM; the
+    8192^3 capture in profiles/ reads 8060 flop per tensor-active cycle)."""
+    return sms * SM_BF16_FLOP_PER_CLK * mhz * 1e6 / 1e12
+
+
+def workload_record(name, sk, dev, pk, steps, warmup, flush):
+    """One of the other configurations (FP32, FP8, grouped, autograd),
+    measured like the sweep (inputs resident, L2 flushed before every timed
+    run, CUDA events, median of `steps`), each next to its data-parallel
+    counterpart.  Returns a record with per-case rows and the roofline of
+    the dominant case."""
     auto, dp = sk.Config(), sk.Config(mode="dp")
     rows = []
-    if args.workload == "fp8":
+    if name == "fp8":
         peak = 2 * pk["bf16"]
         peak_note = "2 x measured bf16 burst (no FP8 measurement available)"
         for i, (M, N, K) in enumerate(workloads.FP8_SHAPES):
@@ -431,17 +468,18 @@ def run_workload(args, world, rank, local):
             xb = workloads.device_normal((N, K), seed=2001 + 2 * i, device=dev)
             qa, sa = sk.quantize_e4m3(xa)
             qb, sb = sk.quantize_e4m3(xb)
+            del xa, xb
             A, Bm = qa.view(torch.float8_e4m3fn), qb.view(torch.float8_e4m3fn).t()
             C = torch.empty(M, N, dtype=torch.bfloat16, device=dev)
             for cfg in (auto, dp):
-                for _ in range(args.warmup):
+                for _ in range(warmup):
                     sk.gemm(A, Bm, C, scale_a=sa, scale_b=sb, config=cfg)
             t = _timed_region(lambda: sk.gemm(A, Bm, C, scale_a=sa, scale_b=sb, config=auto), steps, flush)
             tdp = _timed_region(lambda: sk.gemm(A, Bm, C, scale_a=sa, scale_b=sb, config=dp), steps, flush)
             rows.append((f"{M}x{N}x{K} e4m3", workloads.gemm_flops(M, N, K), t, tdp))
         desc = "FP8 E4M3 per-tensor scaled, FP32 accumulate, BF16 out: " + " ".join(
             f"({m},{n},{k})" for m, n, k in workloads.FP8_SHAPES)
-    elif args.workload == "grouped":
+    elif name == "grouped":
         peak, peak_note = pk["bf16"], "measured bf16 burst"
         shapes = workloads.grouped_shapes(count=64, seed=0)
         As, Bs, Cs = [], [], []
@@ -450,7 +488,7 @@ def run_workload(args, world, rank, local):
             Bs.append(workloads.device_uniform((N, K), seed=3001 + 2 * i, device=dev).t())
             Cs.append(torch.empty(M, N, dtype=torch.bfloat16, device=dev))
         graphs = {}
-        for name, cfg in (("auto", auto), ("dp", dp)):
+        for gname, cfg in (("auto", auto), ("dp", dp)):
             sk.grouped_gemm(As, Bs, Cs, config=cfg)
             s = torch.cuda.Stream()
             s.wait_stream(torch.cuda.current_stream())
@@ -459,7 +497,7 @@ def run_workload(args, world, rank, local):
                 with torch.cuda.graph(g, stream=s):
                     sk.grouped_gemm(As, Bs, Cs, config=cfg)
             torch.cuda.current_stream().wait_stream(s)
-            graphs[name] = g
+            graphs[gname] = g
         # per-problem launches (one graph of 64 launches), the library's default each
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -473,7 +511,7 @@ def run_workload(args, world, rank, local):
         torch.cuda.current_stream().wait_stream(s)
         graphs["separate"] = g
         for gg in graphs.values():
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 gg.replay()
         f = sum(workloads.gemm_flops(*x) for x in shapes)
         t = _timed_region(graphs["auto"].replay, steps, flush)
@@ -483,7 +521,7 @@ def run_workload(args, world, rank, local):
         rows.append(("64 separate launches", f, tsep, tsep))
         desc = ("grouped BF16: 64 problems, M log-uniform [64,4096], N,K from {1024,2048,4096,7168}, "
                 "one persistent launch replayed from a CUDA graph")
-    elif args.workload == "autograd":
+    elif name == "autograd":
         peak, peak_note = pk["bf16"], "measured bf16 burst"
         M, N, K = workloads.AUTOGRAD_SHAPE
         A = workloads.device_uniform((M, K), seed=4000, device=dev).requires_grad_(True)
@@ -497,33 +535,33 @@ def run_workload(args, world, rank, local):
             C.backward(G)
 
         for cfg in (auto, dp):
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 step(cfg)
         f = 3 * workloads.gemm_flops(M, N, K)
         t = _timed_region(lambda: step(auto), steps, flush)
         tdp = _timed_region(lambda: step(dp), steps, flush)
         rows.append((f"{M}x{N}x{K} fwd+bwd", f, t, tdp))
         desc = "autograd BF16 layer: forward C=A*B plus backward dA=dC*B^T, dB=A^T*dC"
-    elif args.workload == "f32":
-        # The library runs this FP32 shape as 3xTF32 on the tensor cores:
-        # three TF32 products per k-step at half the BF16 rate, so its useful
-        # peak is the measured BF16 peak / 2 / 3.  The FFMA kernel's row is
-        # context (not in the totals), against the derived FFMA peak: SMs x
-        # 128 FP32 lanes x 2 flop x the maximum SM clock (2070 MHz).
+    elif name.startswith("f32"):
+        # The library runs FP32 problems with K-major operands as 3xTF32 on
+        # the tensor cores: three TF32 products per k-step at half the BF16
+        # rate, so its useful peak is the measured BF16 peak / 2 / 3.  The
+        # FFMA kernel's row is context (not in the totals), against the
+        # derived FFMA peak: SMs x 128 FP32 lanes x 2 flop x 2.07 GHz.
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak = pk["bf16"] / 2 / 3
         peak_note = (f"3xTF32: {pk['source']} bf16 burst {pk['bf16']} / 2 (TF32 rate) / 3 (products); "
                      f"FFMA row: {sms} SMs x 128 lanes x 2 flop x 2.07 GHz (derived)")
         ffma_peak = sms * 128 * 2 * 2.07e9 / 1e12
         M, N, K = (workloads.FP32_SMALL[x] for x in ("M", "N", "K"))
-        if args.only:
-            M, N, K = (int(x) for x in args.only.split(","))
+        if ":" in name:
+            M, N, K = (int(x) for x in name.split(":", 1)[1].split(","))
         A = workloads.device_uniform((M, K), seed=5000, device=dev, dtype=torch.float32)
         Bm = workloads.device_uniform((N, K), seed=5001, device=dev, dtype=torch.float32).t()
         C = torch.empty(M, N, dtype=torch.float32, device=dev)
         ff, ffdp = sk.Config(f32_kernel="ffma"), sk.Config(mode="dp", f32_kernel="ffma")
         for cfg in (auto, dp, ff, ffdp):
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 sk.gemm(A, Bm, C, config=cfg)
         t = _timed_region(lambda: sk.gemm(A, Bm, C, config=auto), steps, flush)
         tdp = _timed_region(lambda: sk.gemm(A, Bm, C, config=dp), steps, flush)
@@ -534,28 +572,59 @@ def run_workload(args, world, rank, local):
         desc = (f"FP32 {M}x{N}x{K}, A row-major, B column-major, uniform[-1,1]; 128x128 tiles, "
                 "3xTF32 tensor-core kernel (FFMA kernel as context)")
     else:
-        raise ValueError(args.workload)
+        raise ValueError(name)
     if ws_status(sk, dev) != 0:
         raise RuntimeError("device status")
     ctx = ("64 separate", "ffma kernel")   # context rows, not in the totals
-    tot_f = sum(r[1] for r in rows if not r[0].startswith(ctx))
-    tot_t = sum(r[2] for r in rows if not r[0].startswith(ctx))
-    tot_dp = sum(r[3] for r in rows if not r[0].startswith(ctx))
-    value = tot_f / (tot_t / 1e3) / 1e12
-    if rank != 0:
-        return None
+    main = [r for r in rows if not r[0].startswith(ctx)]
+    tot_f = sum(r[1] for r in main)
+    tot_t = sum(r[2] for r in main)
+    tot_dp = sum(r[3] for r in main)
+    dom = max(main, key=lambda r: r[2])
+    achieved = dom[1] / dom[2] / 1e9
     return {
-        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": steps,
-        "warmup": args.warmup, "ms_per_step": round(tot_t, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp8": "e4m3", "f32": "f32"}.get(args.workload, "bf16"), "data": "synthetic",
-        "config": {"workload": desc, "l2": "flushed (write then read 256 MB) before every timed run"},
-        "dp_baseline": {"value": round(tot_f / (tot_dp / 1e3) / 1e12, 2), "unit": UNIT},
+        "workload": desc, "steps": steps, "warmup": warmup,
+        "dtype": {"fp8": "e4m3"}.get(name, "f32" if name.startswith("f32") else "bf16"),
+        "value": round(tot_f / (tot_t / 1e3) / 1e12, 2), "unit": UNIT, "ms": round(tot_t, 4),
+        "dp_baseline": {"value": round(tot_f / (tot_dp / 1e3) / 1e12, 2), "unit": UNIT, "ms": round(tot_dp, 4)},
+        "sk_over_dp": round(tot_dp / tot_t, 3),
         "rows": [{"case": r[0], "ms": round(r[2], 4), "us": round(1e3 * r[2], 2), "dp_us": round(1e3 * r[3], 2),
                   "tflops": round(r[1] / r[2] / 1e9, 2),
                   "pct_peak": round(100 * r[1] / r[2] / 1e9 / (r[4] if len(r) > 4 else peak), 1),
                   "dp_ms": round(r[3], 4),
                   "dp_tflops": round(r[1] / r[3] / 1e9, 1)} for r in rows],
+        "roofline": {"bound": "tensor", "case": dom[0], "achieved": round(achieved, 1), "peak": round(peak, 1),
+                     "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "peak_source": peak_note},
         "peak": {"value": peak, "source": peak_note},
+        "l2": "flushed (write then read 256 MB) before every timed run",
+    }
+
+
+def run_workload(args, world, rank, local):
+    """One of the other configurations on its own (``--workload``)."""
+    import paper_2407_00044_gb300 as sk
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pk = peaks()
+    flushbuf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+
+    def flush():
+        flushbuf.fill_(1.0)
+        torch.sum(flushbuf, dim=0, out=sink)
+
+    steps = max(3, min(args.steps, 50))
+    name = args.workload
+    if name == "f32" and args.only:
+        name = "f32:" + args.only
+    rec = workload_record(name, sk, dev, pk, steps, args.warmup, flush)
+    if rank != 0:
+        return None
+    return {
+        "metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": rec["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": rec["dtype"], "data": "synthetic",
+        "config": {"workload": rec["workload"], "l2": rec["l2"]},
+        "dp_baseline": rec["dp_baseline"], "rows": rec["rows"], "roofline": rec["roofline"], "peak": rec["peak"],
     }
 
 
@@ -688,6 +757,8 @@ def main(argv=None):
     ap.add_argument("--mode", default="auto", choices=["auto", "dp", "sk", "hybrid1", "hybrid2"])
     ap.add_argument("--no-dp", dest="dp", action="store_false", help="skip the data-parallel baseline")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer run")
+    ap.add_argument("--no-configs", dest="configs", action="store_false",
+                    help="skip the FP32 / FP8 / grouped / autograd configurations in the default run")
     ap.add_argument("--no-search", dest="search", action="store_false",
                     help="skip timing every fixed tile/stages/mode candidate of the sweep shapes")
     ap.add_argument("--search-steps", type=int, default=20)

@@ -265,10 +265,17 @@ SK_API sk_status sk_workspace_init(void *ws, size_t ws_bytes, sk_stream_t stream
 SK_API sk_status sk_gemm(const sk_problem *problem, const sk_config *cfg,
                   void *ws, size_t ws_bytes, sk_stream_t stream);
 
-/* `count` independent GEMMs (1 <= count <= 64) in ONE persistent launch.
- * The problems' tiles are concatenated and the decomposition runs over all
- * of them, so Stream-K ranges cross problem boundaries.  All problems must
- * share a_type, b_type and c_type.  Outputs must not overlap. */
+/* `count` independent GEMMs (1 <= count <= 65536) in ONE persistent
+ * launch.  The problems' tiles are concatenated and the decomposition runs
+ * over all of them, so Stream-K ranges cross problem boundaries.  All
+ * problems must share a_type, b_type and c_type (E4M3: one problem per
+ * call).  Outputs must not overlap.  Up to 64 problems travel in the
+ * kernel's parameter block; a larger group keeps its problem table (two
+ * TMA descriptors and the shape of each problem) in the workspace, which
+ * sk_workspace_size then sizes for it, and the call first writes the table
+ * with small copy kernels on `stream` (one per 30 KB of table, each
+ * carrying its bytes in its parameter block, so a captured CUDA graph
+ * replays them too). */
 SK_API sk_status sk_gemm_grouped(const sk_problem *problems, int count,
                           const sk_config *cfg, void *ws, size_t ws_bytes,
                           sk_stream_t stream);
@@ -333,19 +340,28 @@ SK_API const char *sk_last_error(void);
  * Same operands, config and result as sk_gemm, except that tile_n = 0
  * selects 128 here (so every SM fits).  Limit: the plan's workspace must
  * fit in 12 MiB -- 128x128 tiles on up to 191 CTAs, or 128x256 tiles on up
- * to 95 CTAs; larger requests return SK_ERR_WORKSPACE_TOO_SMALL before
- * anything is launched.
+ * to 95 CTAs; the last-arriver fixup needs two partial slots per CTA, so
+ * there 128x128 tiles on up to 95 CTAs.  Larger requests return
+ * SK_ERR_WORKSPACE_TOO_SMALL before anything is launched.
  *
- * All calls share the one array per GPU.  Each call first zeroes its status
- * word and flags on `stream`, so calls ordered on the GPU are independent,
- * but calls that overlap on the GPU (different streams, no ordering between
- * them) race on the array and give undefined results.  The first call on a
- * device looks up the array's device address (once per device, with that
- * device current); make that first call before capturing any stream.
- * Device-side status (timeouts) is not readable through sk_get_status for
- * this call. */
+ * All calls share the one array per GPU.  Each call first zeroes the
+ * array's flag region on `stream`, so calls ordered on the GPU are
+ * independent, but calls that overlap on the GPU (different streams, no
+ * ordering between them) race on the array and give undefined results.
+ * The first call on a device (of this function or of sk_static_ws_status)
+ * looks up the array's device address (once per device, with that device
+ * current); make that first call before capturing any stream.  A device
+ * wait that expires is recorded in the array's status word, which stays
+ * set across later calls until sk_static_ws_status clears it. */
 SK_API sk_status sk_gemm_static_ws(const sk_problem *problem, const sk_config *cfg,
                                    sk_stream_t stream);
+
+/* The device-side status of sk_gemm_static_ws calls on the current device:
+ * synchronise `stream`, read the fixed array's status word (SK_OK, or
+ * SK_ERR_TIMEOUT if a bounded wait of any call since the last clear
+ * expired) into *device_status, and clear it if `clear`.  (The paper has no
+ * counterpart.)  Allocates nothing. */
+SK_API sk_status sk_static_ws_status(sk_stream_t stream, int clear, sk_status *device_status);
 
 /* Library version string. */
 SK_API const char *sk_version(void);

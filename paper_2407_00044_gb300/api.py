@@ -153,21 +153,28 @@ class Workspace:
 
 _ws_lock = threading.Lock()
 _ws_cache: dict = {}
+_ws_retired: list = []
 
 
-def default_workspace(device=None) -> Workspace:
+def default_workspace(device=None, min_bytes: int = 0) -> Workspace:
     """The workspace calls without an explicit one use: one per device and
     stream (the current stream of that device), so GEMMs running on
     different streams at the same time never share partial slots or flags.
-    Calls on one stream are ordered by it and share its workspace."""
+    Calls on one stream are ordered by it and share its workspace.  A call
+    that needs more (a group of more than 64 problems keeps its problem
+    table there) replaces it with a larger one; make such a call once
+    before capturing a CUDA graph, as the allocation cannot be captured."""
     dev = torch.device(device if device is not None else torch.cuda.current_device())
     if dev.index is None:
         dev = torch.device("cuda", torch.cuda.current_device())
     key = (dev.index, torch.cuda.current_stream(dev).cuda_stream)
     with _ws_lock:
         ws = _ws_cache.get(key)
-        if ws is None:
-            ws = Workspace(dev)
+        if ws is None or ws.nbytes < min_bytes:
+            if ws is not None:
+                _ws_retired.append(ws)   # CUDA graphs captured earlier may still use it
+            base = default_workspace_bytes(torch.cuda.get_device_properties(dev).multi_processor_count)
+            ws = Workspace(dev, max(base, int(min_bytes)))
             _ws_cache[key] = ws
         return ws
 
@@ -203,8 +210,17 @@ def grouped_gemm(As, Bs, outs=None, *, alpha: float = 1.0, beta: float = 0.0, C_
     for i in range(n):
         arr[i] = make_problem(As[i], Bs[i], outs[i], C_in=None if C_ins is None else C_ins[i],
                               alpha=alpha, beta=beta)
-    ws = workspace or default_workspace(As[0].device)
     cfg = _cfg(config)
+    if workspace is None:
+        need = 0
+        if n > 64:   # the problem table goes into the workspace
+            nb = ctypes.c_size_t(0)
+            with torch.cuda.device(As[0].device):
+                B.check(B.sk_workspace_size(arr, n, ctypes.byref(cfg), ctypes.byref(nb)), "sk_workspace_size")
+            need = nb.value
+        ws = default_workspace(As[0].device, need)
+    else:
+        ws = workspace
     B.check(B.sk_gemm_grouped(arr, n, ctypes.byref(cfg), ws.ptr, ws.nbytes, _stream()), "sk_gemm_grouped")
     return outs
 

@@ -107,6 +107,7 @@ _SIGNATURES = {
     "sk_plan_unit_items": (_st, [_P(sk_problem), ctypes.c_int, _P(sk_config), ctypes.c_int, ctypes.c_int,
                                  _P(sk_work_item), ctypes.c_int, _P(ctypes.c_int)]),
     "sk_gemm_static_ws": (_st, [_P(sk_problem), _P(sk_config), _vp]),
+    "sk_static_ws_status": (_st, [_vp, ctypes.c_int, _P(ctypes.c_int)]),
     "sk_last_error": (ctypes.c_char_p, []),
     "sk_version": (ctypes.c_char_p, []),
 }
@@ -181,6 +182,10 @@ def sk_plan_unit_items(problems, count, cfg, num_sms, unit, items, max_items, n_
 
 def sk_gemm_static_ws(problem, cfg, stream):
     return load().sk_gemm_static_ws(problem, cfg, stream)
+
+
+def sk_static_ws_status(stream, clear, out):
+    return load().sk_static_ws_status(stream, clear, out)
 
 
 def sk_last_error() -> str:

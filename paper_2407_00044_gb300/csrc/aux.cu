@@ -3,6 +3,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <cstring>
+
 #include "common.cuh"
 
 namespace sk {
@@ -59,7 +61,39 @@ __global__ void quant_kernel(const float *x, int64_t n, uint8_t *q, float *scale
   }
 }
 
+struct UploadBlock {
+  uint4 *dst;
+  uint32_t n16;   // 16-byte words carried
+  uint32_t pad_;
+  uint4 data[UPLOAD_CHUNK_BYTES / 16];
+};
+
+__global__ void upload_kernel(const __grid_constant__ UploadBlock b) {
+  for (uint32_t i = threadIdx.x; i < b.n16; i += blockDim.x) b.dst[i] = b.data[i];
+  // the words may hold tensor maps that later kernels hand to the TMA unit
+  asm volatile("fence.proxy.tensormap::generic.release.gpu;" ::: "memory");
+}
+
 }  // namespace
+
+cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
+  if ((bytes & 15u) || (reinterpret_cast<uintptr_t>(dst) & 15u)) return cudaErrorInvalidValue;
+  const uint8_t *s = static_cast<const uint8_t *>(src);
+  uint8_t *d = static_cast<uint8_t *>(dst);
+  UploadBlock *b = new UploadBlock();
+  cudaError_t e = cudaSuccess;
+  for (size_t off = 0; off < bytes && e == cudaSuccess; off += UPLOAD_CHUNK_BYTES) {
+    const size_t n = bytes - off < (size_t)UPLOAD_CHUNK_BYTES ? bytes - off : (size_t)UPLOAD_CHUNK_BYTES;
+    b->dst = reinterpret_cast<uint4 *>(d + off);
+    b->n16 = (uint32_t)(n / 16);
+    b->pad_ = 0;
+    std::memcpy(b->data, s + off, n);
+    upload_kernel<<<1, 256, 0, st>>>(*b);
+    e = cudaGetLastError();
+  }
+  delete b;
+  return e;
+}
 
 cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N, float beta, int c_is_f32,
                          cudaStream_t st) {

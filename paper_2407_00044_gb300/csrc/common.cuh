@@ -9,7 +9,11 @@
 
 namespace sk {
 
-constexpr int MAXP_GROUPED = 64;      // problems per grouped launch
+// Problems a grouped launch carries inline in its kernel parameter block;
+// larger groups (up to MAX_PROBLEMS) keep their problem table in the
+// caller's workspace (TcParams::gprob / SimtParams::gprob).
+constexpr int MAXP_GROUPED = 64;
+constexpr int MAX_PROBLEMS = 1 << 16;
 constexpr uint32_t STATUS_TIMEOUT = 4;  // == SK_ERR_TIMEOUT
 
 // Device views of the caller's workspace.
@@ -60,6 +64,10 @@ struct SimtParams {
   Sched sched;
   ProbSched ps[MAXP];
   SimtProblem prob[MAXP];
+  // Groups of more than MAXP problems: the tables in global memory (the
+  // inline arrays are then unused); null otherwise.
+  const SimtProblem *gprob;
+  const ProbSched *gps;
   Workspace ws;
   uint64_t timeout_ns;
   int32_t debug_flags;
@@ -93,6 +101,11 @@ struct TcParams {
   TcProblem prob[MAXP];
   CUtensorMap tmap_c[1];   // C of problem 0 (row-major, box {128 B of columns, 32 rows}, 128B swizzle)
   ProbSched ps[MAXP];
+  // Groups of more than MAXP problems: the tables in global memory (the
+  // inline arrays are then unused; the tensor maps were written there by
+  // launch_upload and are acquired by the tensormap proxy before use).
+  const TcProblem *gprob;
+  const ProbSched *gps;
   Sched sched;
   Workspace ws;
   uint64_t timeout_ns;
@@ -145,6 +158,14 @@ int pair_max_clusters(int stages);
 
 cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N,
                          float beta, int c_is_f32, cudaStream_t st);
+
+// Copies `bytes` (a multiple of 16) of host memory to the device address
+// `dst` (16-byte aligned) with kernels that carry the bytes in their
+// parameter blocks (UPLOAD_CHUNK_BYTES per launch): ordered on the stream,
+// nothing allocated, and a captured CUDA graph keeps its own copy of the
+// bytes.  Tensor maps among them are released to the tensormap proxy.
+constexpr int UPLOAD_CHUNK_BYTES = 30720;
+cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t st);
 
 cudaError_t launch_quant_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_out,
                               float *amax_work, cudaStream_t st);

@@ -99,12 +99,17 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
   const int ty = t >> 4, tx = t & 15;
   const int u = blockIdx.x;
   const Sched &S = P.sched;
+  // Problem tables: inline in the parameter block, or, for groups larger
+  // than MAXP, in global memory.
+  const bool gtab = MAXP > 1 && P.gprob != nullptr;
+  const SimtProblem *const probs = gtab ? P.gprob : P.prob;
+  const ProbSched *const pss = gtab ? P.gps : P.ps;
 
   Cursor cur;
   cursor_init(S, u, cur);
   Item w;
-  while (cursor_next(S, P.ps, u, cur, w)) {
-    const SimtProblem &pr = P.prob[w.problem];
+  while (cursor_next(S, pss, u, cur, w)) {
+    const SimtProblem &pr = probs[w.problem];
     const int m0 = w.tm * F32_BM, n0 = w.tn * F32_BN;
     float acc[8][8];
 #pragma unroll
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
       // float4 words from all partials in the fixed order and stores it.
       int o = u, pl = w.peer_last;
       if (w.role == ROLE_PEER) {
-        const ProbSched &q = P.ps[w.problem];
+        const ProbSched &q = pss[w.problem];
         const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
         o = unit_of_iter(S, ts);
         pl = unit_of_iter(S, ts + q.iters - 1);
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(F32_THREADS, 1) sk_simt_f32_kernel(const __gri
       }
       // Count this arrival at the tile's owner o; the CTA completing the
       // count (pl - o earlier arrivals) sums the tile in the fixed order.
-      const ProbSched &q = P.ps[w.problem];
+      const ProbSched &q = pss[w.problem];
       const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
       const int o = unit_of_iter(S, ts);
       const int pl = unit_of_iter(S, ts + q.iters - 1);

@@ -150,13 +150,18 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   constexpr bool X3 = IN == IN_TF32X3;
   constexpr int OP_BYTES = A_BYTES + B_BYTES;
   constexpr int STAGE_BYTES = X3 ? 2 * OP_BYTES : OP_BYTES;
-  constexpr int TX_BYTES = PAIR ? 2 * OP_BYTES : OP_BYTES;   // landing on the leader's barrier
+  // Where a CTA's operand loads complete: on its own `full` barrier (single
+  // CTAs, and 3xTF32 pairs, whose splitting warps wait for their own CTA's
+  // operands), or on the pair leader's (the leader's MMA issuer waits for
+  // both halves there).
+  constexpr bool OWN_FULL = !PAIR || X3;
+  constexpr int TX_BYTES = OWN_FULL ? OP_BYTES : 2 * OP_BYTES;
   constexpr uint32_t TMEM_COLS = 2 * BN;
   constexpr int MN_CHUNK_BYTES = BK * 128;   // one 64-wide MN chunk of an MN-major slice
   constexpr uint32_t IDESC = Tr::IDESC_TYPES | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "tile N");
   static_assert(!PAIR || BN % 64 == 0, "pair tile N");
-  static_assert(!X3 || !PAIR, "3xTF32 runs on single CTAs");
+  static_assert(!X3 || !PAIR || BN == 256, "3xTF32 pairs use 256 x 256 tiles");
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *tempty_bar = tfull_bar + 2;
   uint64_t *done_bar = tempty_bar + 2;
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
-  uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage converted (one per stage)
+  uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage split (one per stage; the leader's in a pair)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(conv_bar + (X3 ? stages : 0));
   volatile uint32_t *abort_flag = tmem_slot + 1;
   volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
@@ -186,6 +191,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   const int slot_id = PAIR ? 2 * u + (int)rank : u;   // workspace slot / flag of this CTA
   const Sched &S = P.sched;
   const uint64_t tmo = P.timeout_ns;
+  // Problem tables: inline in the parameter block, or, for groups larger
+  // than MAXP, in global memory.
+  const bool gtab = MAXP > 1 && P.gprob != nullptr;
+  const TcProblem *const probs = gtab ? P.gprob : P.prob;
+  const ProbSched *const pss = gtab ? P.gps : P.ps;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
@@ -198,8 +208,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     }
     mbar_init(smem_u32(done_bar), 1);
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
-    if constexpr (X3)
-      for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), 4);   // the 4 epilogue warps
+    if constexpr (X3)   // the 4 epilogue warps of this CTA (of both CTAs in a pair)
+      for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), PAIR ? 8 : 4);
     *abort_flag = 0;
     fix_fail[0] = fix_fail[1] = 0;
     fence_barrier_init();
@@ -231,11 +241,14 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      const int np = S.num_problems < MAXP ? S.num_problems : MAXP;
-      for (int p = 0; p < np && p < 4; ++p) {
-        tma_prefetch_desc(&P.prob[p].tmap_a);
-        tma_prefetch_desc(&P.prob[p].tmap_b);
+      if (!gtab) {
+        const int np = S.num_problems < MAXP ? S.num_problems : MAXP;
+        for (int p = 0; p < np && p < 4; ++p) {
+          tma_prefetch_desc(&P.prob[p].tmap_a);
+          tma_prefetch_desc(&P.prob[p].tmap_b);
+        }
       }
+      int acquired = -1;   // global-table problem whose tensor maps this thread has acquired
       int stage = 0;
       uint32_t phase = 0;
       int64_t loads = 0;
@@ -243,8 +256,13 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       cursor_init(S, u, c);
       Item w;
       bool ok = true;
-      while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
-        const TcProblem &pr = P.prob[w.problem];
+      while (ok && !*abort_flag && cursor_next(S, pss, u, c, w)) {
+        const TcProblem &pr = probs[w.problem];
+        if (gtab && w.problem != acquired) {
+          tensormap_acquire(&pr.tmap_a);
+          tensormap_acquire(&pr.tmap_b);
+          acquired = w.problem;
+        }
         const int m0 = w.tm * BM + (int)rank * 128;
         const int n0 = w.tn * BN + (int)rank * B_ROWS;
         // Both operands K-major is the common case: one load per operand,
@@ -257,11 +275,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             break;
           }
           const uint32_t fb = smem_u32(full_bar + stage);
-          if (leader) mbar_arrive_expect_tx(fb, TX_BYTES);
+          if (OWN_FULL || leader) mbar_arrive_expect_tx(fb, TX_BYTES);
           const uint32_t sa = tiles_addr + stage * STAGE_BYTES;
           const uint32_t sb = sa + A_BYTES;
           const int kx = kb * BK;
-          if constexpr (PAIR) {
+          if constexpr (!OWN_FULL) {
             const uint32_t fbl = mapa_shared(fb, 0);   // the leader's barrier
             if (kmaj) {
               tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
@@ -298,7 +316,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                 tma_load_2d(sb, &pr.tmap_b, fb, kx, n0);
               } else {
 #pragma unroll
-                for (int ch = 0; ch < BN / 64; ++ch)
+                for (int ch = 0; ch < B_ROWS / 64; ++ch)
                   tma_load_2d(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fb, n0 + 64 * ch, kx);
               }
             }
@@ -313,10 +331,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       if (!ok) fail();
       // Drain (bounded): every issued TMA load must land before the CTA may
       // exit -- slot s last completed phase `phase` if s < stage, else the
-      // phase before (in a pair, the leader's barrier sees both CTAs'
-      // loads) -- and, on the normal path, every slot must have been
+      // phase before (in a BF16/E4M3 pair, the leader's barrier sees both
+      // CTAs' loads) -- and, on the normal path, every slot must have been
       // released by the MMA's commits.
-      if (leader) {
+      if (OWN_FULL || leader) {
         for (int s = 0; s < stages && s < loads; ++s) {
           const uint32_t par = s < stage ? phase : (phase ^ 1u);
           if (!mbar_wait(smem_u32(full_bar + s), par, tmo)) {
@@ -348,8 +366,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       Item w;
       bool ok = true;
       int nitem = 0;
-      while (ok && !*abort_flag && cursor_next(S, P.ps, u, c, w)) {
-        const TcProblem &pr = P.prob[w.problem];
+      while (ok && !*abort_flag && cursor_next(S, pss, u, c, w)) {
+        const TcProblem &pr = probs[w.problem];
         const uint32_t idesc = IDESC | ((uint32_t)pr.a_mn << 15) | ((uint32_t)pr.b_mn << 16);
         // Operand descriptors of stage 0, k-step 0; a stage / k-step offset is
         // added to the 14-bit start-address field (addresses < 256 KB, so the
@@ -371,7 +389,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
         for (int kb = w.k0; kb < w.k1; ++kb) {
           // 3xTF32 waits for the epilogue warps' conversion of the stage
-          if (!mbar_wait(smem_u32((X3 ? conv_bar : full_bar) + stage), phase, tmo)) {
+          // (in a pair: of both CTAs' halves, arriving on the leader's barrier)
+          const bool got_stage = (X3 && PAIR) ? mbar_wait_cluster(smem_u32(conv_bar + stage), phase, tmo)
+                                              : mbar_wait(smem_u32((X3 ? conv_bar : full_bar) + stage), phase, tmo);
+          if (!got_stage) {
             ok = false;
             break;
           }
@@ -386,9 +407,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
               // a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (the low parts
               // sit OP_BYTES after the high parts)
               constexpr uint64_t LO = (uint64_t)(OP_BYTES >> 4);
-              mma_tf32(d_tmem, ad, bd, idesc, accum);
-              mma_tf32(d_tmem, ad, bd + LO, idesc, 1u);
-              mma_tf32(d_tmem, ad + LO, bd, idesc, 1u);
+              if constexpr (PAIR) {
+                mma_tf32_pair(d_tmem, ad, bd, idesc, accum);
+                mma_tf32_pair(d_tmem, ad, bd + LO, idesc, 1u);
+                mma_tf32_pair(d_tmem, ad + LO, bd, idesc, 1u);
+              } else {
+                mma_tf32(d_tmem, ad, bd, idesc, accum);
+                mma_tf32(d_tmem, ad, bd + LO, idesc, 1u);
+                mma_tf32(d_tmem, ad + LO, bd, idesc, 1u);
+              }
             } else if constexpr (PAIR) {
               if constexpr (IN == IN_BF16)
                 mma_f16_pair(d_tmem, ad, bd, idesc, accum);
@@ -471,8 +498,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     // named barriers.
     int cstage = 0;          // 3xTF32: next stage to convert and its phase
     uint32_t cphase = 0;
-    while (cursor_next(S, P.ps, u, c, w)) {
-      const TcProblem &pr = P.prob[w.problem];
+    while (cursor_next(S, pss, u, c, w)) {
+      const TcProblem &pr = probs[w.problem];
       if constexpr (X3) {
         // Split every loaded FP32 value x of the item's stages: the MMA
         // reads the FP32 container itself as x_hi (kind::tf32 drops the low
@@ -501,7 +528,12 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           }
           fence_proxy_async_smem_cta();   // the generic writes, to the tensor cores' reads
           __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(conv_bar + cstage));
+          if (lane == 0) {
+            if constexpr (PAIR)   // the leader's MMAs read both CTAs' halves
+              mbar_arrive_cluster(mapa_shared(smem_u32(conv_bar + cstage), 0));
+            else
+              mbar_arrive(smem_u32(conv_bar + cstage));
+          }
           if (++cstage == stages) {
             cstage = 0;
             cphase ^= 1u;
@@ -743,7 +775,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         // (bounded) for all of them; then each of its warps sums its units
         // from all the partials in the fixed order and stores them.
         if (w.role == ROLE_PEER) {
-          const ProbSched &q = P.ps[w.problem];
+          const ProbSched &q = pss[w.problem];
           const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
           o = unit_of_iter(S, ts);
           pl = unit_of_iter(S, ts + q.iters - 1);
@@ -918,7 +950,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         } else {
           // Count this arrival at the tile's owner o; the contributor that
           // completes the count (pl - o earlier arrivals) sums the tile.
-          const ProbSched &q = P.ps[w.problem];
+          const ProbSched &q = pss[w.problem];
           const int64_t ts = q.iter_base + (int64_t)w.tile * q.iters;
           o = unit_of_iter(S, ts);
           pl = unit_of_iter(S, ts + q.iters - 1);
@@ -1070,7 +1102,7 @@ cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
 template <int IN, typename OutT, int BN, int MAXP>
 int pair_max_clusters(int stages) {
   auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, true, false>;
-  const int smem = tc_smem_bytes(BN / 2, stages);
+  const int smem = tc_smem_bytes(BN / 2, stages, IN == IN_TF32X3);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(2, 1, 1);

@@ -65,10 +65,24 @@ extern "C" SK_API sk_status sk_gemm_static_ws(const sk_problem *problem, const s
   rc = static_ws_address(&ws);
   if (rc != SK_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // The array keeps whatever the previous call left.  The status word and
-  // the flag region must start at zero; the partial slots are always
-  // written before being read.
-  const size_t header = sk::WS_FLAG_OFFSET + sk::WS_FLAG_BYTES;
-  if (cudaMemsetAsync(ws, 0, header, st) != cudaSuccess) return SK_ERR_CUDA;
+  // The array keeps whatever the previous call left.  The flag region must
+  // start at zero (a call that timed out can leave flags raised); the
+  // partial slots are always written before being read.  The status word
+  // is left alone: a timeout stays recorded until sk_static_ws_status
+  // clears it, like the status word of a caller's workspace.
+  if (cudaMemsetAsync(static_cast<unsigned char *>(ws) + sk::WS_FLAG_OFFSET, 0, sk::WS_FLAG_BYTES, st) !=
+      cudaSuccess)
+    return SK_ERR_CUDA;
   return sk_gemm(problem, &c, ws, kStaticWsBytes, stream);
+}
+
+extern "C" SK_API sk_status sk_static_ws_status(sk_stream_t stream, int clear, sk_status *device_status) {
+  if (!device_status) return SK_ERR_INVALID_ARG;
+  void *ws = nullptr;
+  sk_status rc = static_ws_address(&ws);
+  if (rc != SK_OK) return rc;
+  // The status word is the first word of the array (the workspace layout
+  // every kernel uses); reading it through sk_get_status keeps one
+  // definition of how a status word is read and cleared.
+  return sk_get_status(ws, kStaticWsBytes, stream, clear, device_status);
 }

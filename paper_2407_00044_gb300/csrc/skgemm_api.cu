@@ -208,12 +208,13 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.BM = d.tile_m;
   if (d.f32_kernel < SK_F32_AUTO || d.f32_kernel > SK_F32_TF32X3) return SK_ERR_INVALID_ARG;
   if (fam == FAM_F32 && d.f32_kernel == SK_F32_TF32X3) {
-    // 3xTF32 on the tensor cores: 128 x 128 tiles, 32-deep k-blocks, each
-    // stage twice the loaded bytes (high and low parts)
-    if (r.pair) return SK_ERR_UNSUPPORTED;
-    if (d.tile_n != 0 && d.tile_n != 128) return SK_ERR_UNSUPPORTED;
+    // 3xTF32 on the tensor cores: 128 x 128 tiles on one CTA or 256 x 256
+    // tiles on a CTA pair (each CTA holds 128 rows of A and 128 of B),
+    // 32-deep k-blocks, each stage twice the loaded bytes (high and low parts)
+    const int bn = r.pair ? 256 : 128;
+    if (d.tile_n != 0 && d.tile_n != bn) return SK_ERR_UNSUPPORTED;
     r.tc32 = true;
-    r.BN = 128;
+    r.BN = bn;
     r.BK = 32;
     const int max_stages = (227 * 1024 - 1024 - 512 - EPI_STAGE_BYTES) / (2 * (128 * 128 + 128 * 128));
     r.stages = d.stages ? d.stages : max_stages;
@@ -262,10 +263,23 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
 // Workspace bytes (layout in common.cuh): the status word, the fixed flag
 // region, and per CTA one partial slot (128 rows x BN FP32); the
 // last-arriver fixup adds a second slot per CTA.
-size_t ws_bytes_for(const Cfg &c) {
+size_t ws_base_bytes(const Cfg &c) {
   const size_t slots = (size_t)c.ctas() * 128 * c.BN * 4;
   return WS_FLAG_OFFSET + WS_FLAG_BYTES + (c.fixup == FIXUP_LAST_ARRIVER ? 2 : 1) * slots;
 }
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Groups of more than MAXP_GROUPED problems keep their problem table in the
+// workspace, after the partial slots: the kernel's per-problem records
+// (tensor maps included), then the per-problem schedule records.
+size_t table_bytes(const Cfg &c, size_t nprob) {
+  if (nprob <= (size_t)MAXP_GROUPED) return 0;
+  const size_t rec = (c.fam == FAM_F32 && !c.tc32) ? sizeof(SimtProblem) : sizeof(TcProblem);
+  return round256(nprob * rec) + round256(nprob * sizeof(ProbSched));
+}
+
+size_t ws_bytes_for(const Cfg &c, size_t nprob = 0) { return ws_base_bytes(c) + table_bytes(c, nprob); }
 
 Workspace carve(void *ws, const Cfg &c) {
   uint8_t *b = static_cast<uint8_t *>(ws);
@@ -385,6 +399,10 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // epilogue warps also do the split, so an epilogue does not overlap the
 // next item's MMAs).
 #define TF32X3_COEFFS 430.0, 900.0, 5160.0, 4500.0, 3020.0, 0.0, 3210.0, 790.0
+// 3xTF32 on CTA pairs (256 x 256 tiles): twelve M = 256 TF32 MMAs per
+// 32-deep k-block (1536 cycles), the split spread over both CTAs' epilogue
+// warps.
+#define TF32X3_PAIR_COEFFS 900.0, 1190.0, 8500.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0
 
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
@@ -399,7 +417,7 @@ struct ModelCoeffs {
 };
 
 ModelCoeffs model_coeffs(const Cfg &c) {
-  if (c.fam == FAM_F32 && c.tc32) return {TF32X3_COEFFS, false};
+  if (c.fam == FAM_F32 && c.tc32) return c.pair ? ModelCoeffs{TF32X3_PAIR_COEFFS, false} : ModelCoeffs{TF32X3_COEFFS, false};
   if (c.fam == FAM_F32) return {1700.0, 500.0, 6000.0, 1000.0, 2000.0, 1000.0, 1000.0, 1000.0, true};
   if (c.pair && c.BN == 128) return {PAIR128_COEFFS, false};
   if (c.pair) return {302.0, 1190.0, 5270.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0, false};
@@ -651,10 +669,13 @@ sk_status encode_operand(EncodeTiledFn enc, CUtensorMap *m, const void *base, sk
 }
 
 static_assert(sizeof(TcParams<MAXP_GROUPED>) <= 32000, "kernel parameter block too large");
+// table records are uploaded in whole 16-byte words
+static_assert(sizeof(TcProblem) % 16 == 0 && sizeof(SimtProblem) % 16 == 0 && sizeof(ProbSched) % 16 == 0,
+              "problem records must be multiples of 16 bytes");
 
 template <int MAXP>
 sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, const Cfg &c, Workspace ws,
-                           cudaStream_t st) {
+                           void *table, cudaStream_t st) {
   EncodeTiledFn enc;
   sk_status rc = encoder(&enc);
   if (rc != SK_OK) return rc;
@@ -662,9 +683,15 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   TcParams<MAXP> *P = new TcParams<MAXP>();
   std::memset(P, 0, sizeof(*P));
   const size_t np = probs.size();
+  // More problems than the parameter block holds: build the records on the
+  // host and upload them to the workspace's table region.
+  const bool gtab = np > (size_t)MAXP;
+  std::vector<TcProblem> big(gtab ? np : 0);
+  std::vector<ProbSched> big_ps(gtab ? np : 0);
+  if (gtab) std::memset(static_cast<void *>(big.data()), 0, np * sizeof(TcProblem));
   for (size_t i = 0; i < np; ++i) {
     const Norm &n = probs[i];
-    TcProblem &tp = P->prob[i];
+    TcProblem &tp = gtab ? big[i] : P->prob[i];
     const bool a_k = n.a_layout == SK_ROW_MAJOR;   // A(i,k) at A[i*lda + k]
     const bool b_k = n.b_layout == SK_COL_MAJOR;   // B(k,j) at B[k + j*ldb]
     rc = encode_operand(enc, &tp.tmap_a, n.A, n.in_type, a_k, n.M, n.K, n.lda, 128, c.BK);
@@ -703,7 +730,22 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
     tp.c_vec = aligned16(n.C) && (n.beta == 0.f || aligned16(n.C_in)) && ((n.ldc * ces) % 16 == 0);
     tp.scale_a = n.sa;
     tp.scale_b = n.sb;
-    P->ps[i] = pl.ps[i];
+    if (gtab)
+      big_ps[i] = pl.ps[i];
+    else
+      P->ps[i] = pl.ps[i];
+  }
+  if (gtab) {
+    uint8_t *tb = static_cast<uint8_t *>(table);
+    const size_t rec_bytes = round256(np * sizeof(TcProblem));
+    cudaError_t ue = launch_upload(tb, big.data(), np * sizeof(TcProblem), st);
+    if (ue == cudaSuccess) ue = launch_upload(tb + rec_bytes, big_ps.data(), np * sizeof(ProbSched), st);
+    if (ue != cudaSuccess) {
+      delete P;
+      return cuda_err(ue, "problem table upload");
+    }
+    P->gprob = reinterpret_cast<const TcProblem *>(tb);
+    P->gps = reinterpret_cast<const ProbSched *>(tb + rec_bytes);
   }
   P->sched = pl.s;
   P->ws = ws;
@@ -728,7 +770,8 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
       e = f32out ? launch_tc<IN_BF16, float, 128, MAXP, false>(*P, pl.grid, st)
                  : launch_tc<IN_BF16, __nv_bfloat16, 128, MAXP, false>(*P, pl.grid, st);
   } else if (c.fam == FAM_F32) {
-    e = launch_tc<IN_TF32X3, float, 128, MAXP, false>(*P, pl.grid, st);
+    e = c.pair ? launch_tc<IN_TF32X3, float, 256, MAXP, true>(*P, pl.grid, st)
+               : launch_tc<IN_TF32X3, float, 128, MAXP, false>(*P, pl.grid, st);
   } else if (c.fam == FAM_E4M3) {
     if constexpr (MAXP == 1) {
       if (c.pair)
@@ -751,12 +794,16 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
 
 template <int MAXP>
 sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, const Cfg &c, Workspace ws,
-                            cudaStream_t st) {
+                            void *table, cudaStream_t st) {
   SimtParams<MAXP> *P = new SimtParams<MAXP>();
   std::memset(P, 0, sizeof(*P));
-  for (size_t i = 0; i < probs.size(); ++i) {
+  const size_t np = probs.size();
+  const bool gtab = np > (size_t)MAXP;
+  std::vector<SimtProblem> big(gtab ? np : 0);
+  std::vector<ProbSched> big_ps(gtab ? np : 0);
+  for (size_t i = 0; i < np; ++i) {
     const Norm &n = probs[i];
-    SimtProblem &sp = P->prob[i];
+    SimtProblem &sp = gtab ? big[i] : P->prob[i];
     sp.A = static_cast<const float *>(n.A);
     sp.B = static_cast<const float *>(n.B);
     sp.C_in = static_cast<const float *>(n.C_in);
@@ -786,7 +833,22 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
     sp.a_vec = aligned16(n.A) && (n.lda % 4 == 0);
     sp.b_vec = aligned16(n.B) && (n.ldb % 4 == 0);
     sp.c_vec = aligned16(n.C) && (n.beta == 0.f || aligned16(n.C_in)) && (n.ldc % 4 == 0);
-    P->ps[i] = pl.ps[i];
+    if (gtab)
+      big_ps[i] = pl.ps[i];
+    else
+      P->ps[i] = pl.ps[i];
+  }
+  if (gtab) {
+    uint8_t *tb = static_cast<uint8_t *>(table);
+    const size_t rec_bytes = round256(np * sizeof(SimtProblem));
+    cudaError_t ue = launch_upload(tb, big.data(), np * sizeof(SimtProblem), st);
+    if (ue == cudaSuccess) ue = launch_upload(tb + rec_bytes, big_ps.data(), np * sizeof(ProbSched), st);
+    if (ue != cudaSuccess) {
+      delete P;
+      return cuda_err(ue, "problem table upload");
+    }
+    P->gprob = reinterpret_cast<const SimtProblem *>(tb);
+    P->gps = reinterpret_cast<const ProbSched *>(tb + rec_bytes);
   }
   P->sched = pl.s;
   P->ws = ws;
@@ -848,7 +910,7 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
       return SK_OK;
     }
   }
-  const bool pair_ok = fam != FAM_F32 && (d->num_ctas > 0 ? d->num_ctas : sms) >= 2;
+  const bool pair_ok = (fam != FAM_F32 || d->f32_kernel == SK_F32_TF32X3) && (d->num_ctas > 0 ? d->num_ctas : sms) >= 2;
   std::vector<int> tms, tns;
   std::vector<sk_mode> modes;
   if (free_tile_m) {
@@ -883,6 +945,11 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
         }
         PlanOut pl;
         build_plan(work, idx, c, &pl);
+        if (c.fixup == FIXUP_SPLIT && !split_eligible(pl)) {
+          // an explicit split reduce needs a plan it can run
+          last_rc = fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
+          continue;
+        }
         double ns = predict_ns(work, pl, c);
         if (ns < best * 0.999) {   // keep the earlier candidate on near-ties
           best = ns;
@@ -1024,8 +1091,8 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
 // (cached per device and variant).
 int pair_clusters(int dev, const Cfg &c, bool f32out, bool grouped) {
   static std::mutex mu;
-  static int cache[64][2][2][2][2][16] = {};
-  const int fi = c.fam == FAM_E4M3 ? 1 : 0;
+  static int cache[64][3][2][2][2][16] = {};
+  const int fi = c.fam == FAM_E4M3 ? 1 : c.fam == FAM_F32 ? 2 : 0;
   const int bi = c.BN == 128 ? 1 : 0;
   const int st = c.stages & 15;
   std::lock_guard<std::mutex> lk(mu);
@@ -1046,6 +1113,9 @@ int pair_clusters(int dev, const Cfg &c, bool f32out, bool grouped) {
       else
         n = f32out ? pair_max_clusters<IN_BF16, float, 256, 1>(c.stages)
                    : pair_max_clusters<IN_BF16, __nv_bfloat16, 256, 1>(c.stages);
+    } else if (c.fam == FAM_F32) {
+      n = grouped ? pair_max_clusters<IN_TF32X3, float, 256, MAXP_GROUPED>(c.stages)
+                  : pair_max_clusters<IN_TF32X3, float, 256, 1>(c.stages);
     } else {
       n = f32out ? pair_max_clusters<IN_E4M3, float, 256, 1>(c.stages)
                  : pair_max_clusters<IN_E4M3, __nv_bfloat16, 256, 1>(c.stages);
@@ -1088,7 +1158,7 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   }
   if (!work.empty()) {
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return SK_ERR_INVALID_ARG;
-    if (ws_bytes < ws_bytes_for(c)) return SK_ERR_WORKSPACE_TOO_SMALL;
+    if (ws_bytes < ws_bytes_for(c, work.size())) return SK_ERR_WORKSPACE_TOO_SMALL;
   }
   for (const Norm &n : scale_only) {
     rc = cuda_err(launch_scale(n.C, n.C_in, n.ldc, n.M, n.N, n.beta, n.c_type == SK_F32, st), "k=0 scale launch");
@@ -1100,10 +1170,13 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   if (c.fixup == FIXUP_SPLIT && !split_eligible(pl))
     return fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
   Workspace w = carve(ws, c);
+  void *table = static_cast<uint8_t *>(ws) + ws_base_bytes(c);   // used for groups beyond MAXP_GROUPED
   if (c.fam == FAM_F32 && !c.tc32) {
-    return grouped ? launch_f32_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_f32_family<1>(work, pl, c, w, st);
+    return grouped ? launch_f32_family<MAXP_GROUPED>(work, pl, c, w, table, st)
+                   : launch_f32_family<1>(work, pl, c, w, table, st);
   }
-  return grouped ? launch_tc_family<MAXP_GROUPED>(work, pl, c, w, st) : launch_tc_family<1>(work, pl, c, w, st);
+  return grouped ? launch_tc_family<MAXP_GROUPED>(work, pl, c, w, table, st)
+                 : launch_tc_family<1>(work, pl, c, w, table, st);
 }
 
 // Plan for queries: honours num_sms > 0 without touching a device (the
@@ -1120,7 +1193,7 @@ sk_status plan_for_query(const sk_problem *problems, int count, const sk_config 
   }
   std::vector<Norm> work;
   std::vector<int> idx;
-  sk_status rc = prepare(problems, count, cfg, sms, MAXP_GROUPED, c, &work, &idx, nullptr);
+  sk_status rc = prepare(problems, count, cfg, sms, MAX_PROBLEMS, c, &work, &idx, nullptr);
   if (rc != SK_OK) return rc;
   if (c->pair && dev >= 0 && !work.empty()) {
     const int maxc = pair_clusters(dev, *c, work[0].c_type == SK_F32, count > 1);
@@ -1159,7 +1232,7 @@ sk_status sk_workspace_size(const sk_problem *problems, int count, const sk_conf
   PlanOut pl;
   sk_status rc = plan_for_query(problems, count, cfg, cfg && cfg->num_ctas > 0 ? cfg->num_ctas : 0, &c, &pl);
   if (rc != SK_OK) return rc;
-  *bytes = ws_bytes_for(c);
+  *bytes = ws_bytes_for(c, (size_t)pl.s.num_problems);
   return SK_OK;
 }
 
@@ -1174,7 +1247,7 @@ sk_status sk_gemm(const sk_problem *problem, const sk_config *cfg, void *ws, siz
 
 sk_status sk_gemm_grouped(const sk_problem *problems, int count, const sk_config *cfg, void *ws, size_t ws_bytes,
                           sk_stream_t stream) {
-  return run(problems, count, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), MAXP_GROUPED);
+  return run(problems, count, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), MAX_PROBLEMS);
 }
 
 sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc, void *dA, int64_t ldda, void *dB,
@@ -1227,7 +1300,7 @@ sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc, 
     pr[n++] = p;
   }
   if (n == 0) return SK_OK;
-  return run(pr, n, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), MAXP_GROUPED);
+  return run(pr, n, cfg, ws, ws_bytes, reinterpret_cast<cudaStream_t>(stream), MAX_PROBLEMS);
 }
 
 sk_status sk_quantize_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_out, float *amax_work,
@@ -1274,7 +1347,7 @@ sk_status sk_plan_query(const sk_problem *problems, int count, const sk_config *
   out->sk_iters = pl.s.sk_iters;
   out->iters_per_unit = pl.s.q;
   out->extra_units = pl.s.r;
-  out->workspace_bytes = ws_bytes_for(c);
+  out->workspace_bytes = ws_bytes_for(c, (size_t)pl.s.num_problems);
   out->predicted_us = pl.predicted_ns * 1e-3;
   out->fixup = c.fixup == FIXUP_SPLIT ? SK_FIXUP_SPLIT : c.fixup == FIXUP_LAST_ARRIVER ? SK_FIXUP_LAST_ARRIVER
                                                                                          : SK_FIXUP_OWNER;

@@ -140,8 +140,10 @@ def test_split_reduce_eligibility(sk):
     info = sk.plan(f32, num_sms=152)
     assert info.num_ctas % info.tiles == 0
     if info.fixup == B.SK_FIXUP_SPLIT:
+        ctas = info.num_ctas * (2 if info.tile_m == 256 else 1)
+        same = sk.Config(mode="sk", num_ctas=ctas, tile_m=info.tile_m, tile_n=info.tile_n, fixup="split")
         for u in range(info.num_ctas):
-            its = sk.unit_items(f32, u, sk.Config(mode="sk", num_ctas=info.num_ctas), num_sms=152)
+            its = sk.unit_items(f32, u, same, num_sms=152)
             assert len(its) == 1
 
 
@@ -303,9 +305,13 @@ def test_f32_kernel_choice(sk):
         with pytest.raises(sk.SkError):
             sk.plan(p, sk.Config(f32_kernel="tf32x3"), num_sms=152)
     assert _q(sk, kmaj, {"f32_kernel": 3})[0] == B.SK_ERR_INVALID_ARG
-    # the 3xTF32 tile is 128 x 128 on single CTAs
+    # the 3xTF32 tile is 128 x 128 on single CTAs or 256 x 256 on CTA pairs
+    pair = sk.plan(kmaj, sk.Config(f32_kernel="tf32x3", tile_m=256), num_sms=152)
+    assert (pair.tile_m, pair.tile_n, pair.tile_k, pair.stages) == (256, 256, 32, 3)
     with pytest.raises(sk.SkError):
-        sk.plan(kmaj, sk.Config(f32_kernel="tf32x3", tile_m=256), num_sms=152)
+        sk.plan(kmaj, sk.Config(f32_kernel="tf32x3", tile_m=256, tile_n=128), num_sms=152)
+    with pytest.raises(sk.SkError):
+        sk.plan(kmaj, sk.Config(f32_kernel="ffma", tile_m=256), num_sms=152)
 
 
 def test_tile_aligned_unit_count(sk):
@@ -431,3 +437,30 @@ def test_library_split_choice_on_random_problem_sets(sk):
             assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
             assert ranges[-1][1] == -(-shapes[p][2] // info.tile_k)
     assert picked > 0
+
+
+def test_workspace_size_large_groups(sk):
+    """Up to 64 problems travel in the kernel's parameter block; a larger
+    group's problem table is sized into the workspace (growing with the
+    count), and more than 65536 problems are refused."""
+    B = sk.binding
+    n = ctypes.c_size_t(0)
+    c = sk.api._cfg({"num_ctas": 148, "tile_m": 128, "tile_n": 128})
+
+    def size(count):
+        arr = (B.sk_problem * count)(*[sk.shape_problem(64 + i, 128, 256) for i in range(count)])
+        assert B.sk_workspace_size(arr, count, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+        return n.value
+
+    base = 256 + 4096 + 148 * 128 * 128 * 4
+    assert size(1) == base and size(64) == base
+    s65, s256 = size(65), size(256)
+    assert base < s65 < s256
+    assert (s65 - base) % 256 == 0 and (s256 - base) % 256 == 0
+    # the FFMA kernel's records are smaller than the tensor-core ones (no tensor maps)
+    f = sk.api._cfg({"num_ctas": 148, "f32_kernel": "ffma"})
+    arr = (B.sk_problem * 256)(*[sk.shape_problem(64 + i, 128, 256, dtype="f32") for i in range(256)])
+    assert B.sk_workspace_size(arr, 256, ctypes.byref(f), ctypes.byref(n)) == B.SK_OK
+    assert base < n.value < s256
+    big = (B.sk_problem * 65537)()
+    assert B.sk_workspace_size(big, 65537, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_INVALID_ARG

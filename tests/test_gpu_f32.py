@@ -186,3 +186,70 @@ def test_tf32x3_grouped(m):
     assert m.default_workspace(d).status() == 0
     for o, r, sh in zip(outs, refs, shapes):
         assert np.array_equal(to_np(o), r), sh
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_tf32x3_pair_exact_and_bound(m, mode):
+    """3xTF32 on CTA pairs (256 x 256 tiles, each CTA splitting its own half
+    of the operands, the leader's MMAs reading both): small integers give the
+    exact C (every partial sum is an integer below 2^24), random inputs stay
+    inside the FP32 bound, ragged edges included."""
+    for i, (M, N, K) in enumerate([(384, 384, 2048), (600, 520, 1028), (257, 129, 4096)]):
+        a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=60 + i, dist="int")
+        ref, _ = oracle.gemm(a, b)
+        c = _run(m, a, b, config=m.Config(mode=mode, tile_m=256, min_iters_per_unit=1, f32_kernel="tf32x3"))
+        assert np.array_equal(to_np(c), ref), (M, N, K, mode)
+        a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=70 + i)
+        c = _run(m, a, b, config=m.Config(mode=mode, tile_m=256, f32_kernel="tf32x3"))
+        assert_within_bound(c, a, b, what=f"tf32x3 pair {(M, N, K)} {mode}")
+
+
+def test_tf32x3_pair_fixups_bitwise_and_units(m):
+    """The three fixup protocols give the same bits on pairs, and every
+    pair count gives the exact integer result."""
+    d = dev()
+    sms = torch.cuda.get_device_properties(d).multi_processor_count
+    M, N, K = 512, 512, 8192          # 4 pair tiles of 256 k-blocks
+    a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=80)
+    ad, bd = a.to(d), b.to(d)
+    outs = {}
+    for fx in ("owner", "last_arriver", "split"):
+        # 4 tiles x 16 pairs: ranges of 16 of the 256 k-blocks (split-eligible)
+        cfg = m.Config(mode="sk", tile_m=256, num_ctas=128, fixup=fx, f32_kernel="tf32x3")
+        outs[fx] = m.gemm(ad, bd, config=cfg)
+        assert m.default_workspace(d).status() == 0
+    assert torch.equal(outs["owner"], outs["last_arriver"]) and torch.equal(outs["owner"], outs["split"])
+    assert_within_bound(outs["owner"], a, b, what="tf32x3 pair fixups")
+    ai, bi = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=81, dist="int")
+    ref, _ = oracle.gemm(ai, bi)
+    for g in sorted({2, 6, 14, sms // 2, sms - 2, sms}):
+        c = _run(m, ai, bi, config=m.Config(mode="sk", tile_m=256, num_ctas=g, min_iters_per_unit=1,
+                                            f32_kernel="tf32x3"))
+        assert np.array_equal(to_np(c), ref), g
+
+
+def test_tf32x3_pair_timeout_and_grouped(m):
+    """Bounded waits on pairs expire cleanly (status word, usable context),
+    and grouped FP32 problems run on pair tiles."""
+    d = dev()
+    a, b = workloads.gemm_inputs(384, 384, 2048, dtype="f32", seed=82)
+    ad, bd = a.to(d), b.to(d)
+    ws = m.Workspace(d)
+    cfg = dict(mode="sk", tile_m=256, f32_kernel="tf32x3")
+    m.gemm(ad, bd, config=m.Config(timeout_ns=50_000_000, debug_flags=1, **cfg), workspace=ws)
+    assert ws.status(clear=True) == m.binding.SK_ERR_TIMEOUT
+    m.binding.check(m.binding.sk_workspace_init(ws.ptr, ws.nbytes, None))
+    c = m.gemm(ad, bd, config=m.Config(**cfg), workspace=ws)
+    assert ws.status() == 0
+    assert_within_bound(c, a, b, what="tf32x3 pair after timeout")
+    shapes = [(256, 128, 512), (100, 300, 64), (384, 384, 2048), (1, 8, 4)]
+    As, Bs, refs = [], [], []
+    for i, (M, N, K) in enumerate(shapes):
+        a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=90 + i, dist="int")
+        As.append(a.to(d))
+        Bs.append(same_strides(b, d))
+        refs.append(oracle.gemm(a, b)[0])
+    outs = m.grouped_gemm(As, Bs, config=m.Config(mode="sk", tile_m=256, f32_kernel="tf32x3"))
+    assert m.default_workspace(d).status() == 0
+    for o, r, sh in zip(outs, refs, shapes):
+        assert np.array_equal(to_np(o), r), sh

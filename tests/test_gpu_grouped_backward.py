@@ -153,3 +153,80 @@ def test_autograd_matches_oracle(m):
     assert_within_bound(C, a, b, out="bf16", what="forward")
     assert_within_bound(A.grad, g, b.t(), out="bf16", what="dA")
     assert_within_bound(Bm.grad, a.t(), g, out="bf16", what="dB")
+
+
+def _many_problems(count, seed, dtype="bf16"):
+    shapes = workloads.grouped_shapes(count=count, seed=seed, m_lo=16, m_hi=512,
+                                      nk_choices=(64, 128, 256, 512, 1024))
+    d = dev()
+    As, Bs, refs = [], [], []
+    for i, (M, N, K) in enumerate(shapes):
+        a, b = workloads.gemm_inputs(M, N, K, dtype=dtype, seed=1000 + 7 * seed + i, dist="int")
+        As.append(a.to(d))
+        Bs.append(b.to(d))
+        refs.append(oracle.gemm(a, b)[0])
+    return shapes, As, Bs, refs
+
+
+def test_grouped_256_problems_graph(m):
+    """256 uneven problems in ONE persistent launch: more than the kernel's
+    parameter block carries, so the problem table (tensor maps included)
+    goes to the workspace, written by copy kernels on the stream.  Captured
+    in a CUDA graph and replayed; small-integer inputs make every result
+    exact, so each problem is compared with the oracle in full."""
+    d = dev()
+    shapes, As, Bs, refs = _many_problems(256, seed=1)
+    outs = [torch.empty(a.shape[0], b.shape[1], dtype=torch.float32, device=d) for a, b in zip(As, Bs)]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        m.grouped_gemm(As, Bs, outs)      # first call outside the capture (sizes s's workspace)
+        torch.cuda.synchronize()
+        for i, (o, r) in enumerate(zip(outs, refs)):
+            assert np.array_equal(to_np(o), r), ("direct", i, shapes[i])
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            m.grouped_gemm(As, Bs, outs)
+    for o in outs:
+        o.fill_(float("nan"))
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        assert m.default_workspace(d).status() == 0
+    for i, (o, r) in enumerate(zip(outs, refs)):
+        assert np.array_equal(to_np(o), r), ("graph", i, shapes[i])
+
+
+@pytest.mark.parametrize("tile_m,mode", [(128, "sk"), (256, "hybrid2"), (256, "dp")])
+def test_grouped_many_problems_tiles_modes(m, tile_m, mode):
+    """100 problems (table in the workspace) on both unit shapes and modes,
+    and the workspace-size contract: one byte short is refused."""
+    d = dev()
+    shapes, As, Bs, refs = _many_problems(100, seed=2)
+    cfg = m.Config(mode=mode, tile_m=tile_m)
+    outs = m.grouped_gemm(As, Bs, out_dtype=torch.float32, config=cfg)
+    assert m.default_workspace(d).status() == 0
+    for i, (o, r) in enumerate(zip(outs, refs)):
+        assert np.array_equal(to_np(o), r), (tile_m, mode, i, shapes[i])
+    B = m.binding
+    arr = (B.sk_problem * len(As))(*[m.make_problem(a, b, o) for a, b, o in zip(As, Bs, outs)])
+    import ctypes
+    need = ctypes.c_size_t(0)
+    c = cfg.to_c()
+    B.check(B.sk_workspace_size(arr, len(As), ctypes.byref(c), ctypes.byref(need)))
+    small = m.Workspace(d, need.value - 256)
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert B.sk_gemm_grouped(arr, len(As), ctypes.byref(c), small.ptr, small.nbytes, st) == \
+        B.SK_ERR_WORKSPACE_TOO_SMALL
+
+
+@pytest.mark.parametrize("f32k", ["ffma", "tf32x3"])
+def test_grouped_many_problems_fp32(m, f32k):
+    """FP32 groups beyond the parameter block, on both FP32 kernels."""
+    d = dev()
+    shapes, As, Bs, refs = _many_problems(80, seed=3, dtype="f32")
+    outs = m.grouped_gemm(As, Bs, config=m.Config(mode="hybrid2", f32_kernel=f32k))
+    assert m.default_workspace(d).status() == 0
+    for i, (o, r) in enumerate(zip(outs, refs)):
+        assert np.array_equal(to_np(o), r), (f32k, i, shapes[i])
