@@ -186,13 +186,37 @@ typedef struct {
                                 0 = default 8, at most 64 */
     sk_fixup fixup;          /* partial-sum fixup protocol; default SK_FIXUP_OWNER */
     sk_f32_kernel f32_kernel;/* FP32 problems only; default SK_F32_AUTO */
+    uint32_t *coverage;      /* optional DEVICE buffer of sk_plan_info.coverage_words
+                                words, zeroed by the caller: the kernel counts
+                                which unit ran each MAC-loop iteration and which
+                                unit stored each 32 x 32 block of C (layout
+                                under SK_COVERAGE below).  Tensor-core kernels
+                                only (BF16 single and grouped, FP32 as 3xTF32
+                                single); ignored elsewhere.  A debug variant:
+                                NULL = the normal kernels run */
 } sk_config;
+
+/* Coverage counts (sk_config.coverage), after the schedule the paper's
+ * Background and Methodology describe: every (tile, k-block) MAC-loop
+ * iteration is computed by exactly one unit, and every output element is
+ * stored exactly once.  Word layout, for the problems with m, n, k >= 1 in
+ * the caller's order, tiles of each problem in row-major tile order (before
+ * rasterisation), k-blocks of tile_k:
+ *   [0, total_iters)  word  iter_base(p) + tile * iters(p) + k_block
+ *   then per global tile (tiles of all problems concatenated),
+ *   (tile_m / 32) * (tile_n / 32) words, one per 32 x 32 block of the tile
+ *   (block = (row / 32) * (tile_n / 32) + col / 32 within the tile).
+ * Each visit adds SK_COVERAGE_VISIT(unit) (unit = CTA, or CTA pair when
+ * tile_m == 256): after a correct call every word equals
+ * SK_COVERAGE_VISIT(u) for one unit u, so (word & 0xff) counts the visits
+ * and (word >> 8) - 1 names the unit. */
+#define SK_COVERAGE_VISIT(unit) (1u + (((uint32_t)(unit) + 1u) << 8))
 
 /* Timeline trace layout: CTA c owns entries [c*SK_TRACE_ENTRIES,
  * (c+1)*SK_TRACE_ENTRIES), each two uint64: (event << 32 | item index) and
  * %globaltimer in ns.  Entries 0..47 are written by the MMA issuer, 48..111
  * by the epilogue, 112..115 by the roles' lead threads, 116..121 by the
- * epilogue's fixup/spill/split detail; unused entries keep
+ * epilogue's fixup/spill/split detail, 122 at kernel entry; unused entries keep
  * the caller's contents (zero the buffer first). */
 #define SK_TRACE_ENTRIES 128
 #define SK_TRACE_BYTES_PER_CTA (SK_TRACE_ENTRIES * 16)
@@ -206,6 +230,7 @@ enum {
     SK_EV_EPI_END = 7,     /* item: epilogue done (stores issued / flag raised) */
     SK_EV_END = 8,         /* a role is done (item = 0 producer, 1 MMA issuer,
                               2 epilogue); the CTA ends at the latest of them */
+    SK_EV_ENTRY = 9,       /* the CTA entered the kernel (before any set-up) */
     SK_EV_FIX_ISSUE = 11,  /* last-item fixup: partial copies issued */
     SK_EV_FIX_FIRST = 12,  /*   first staged partial chunk arrived */
     SK_EV_FIX_LAST = 13,   /*   last chunk of the first batch arrived */
@@ -231,6 +256,7 @@ typedef struct {
     size_t workspace_bytes;
     double predicted_us;     /* the library's runtime-model estimate of the call */
     sk_fixup fixup;          /* the fixup protocol the call uses */
+    int64_t coverage_words;  /* uint32 words a sk_config.coverage buffer needs */
 } sk_plan_info;
 
 /* One unit of work of one CTA, in the order that CTA processes it. */

@@ -32,6 +32,7 @@ class Config:
     raster_group: int = 0   # rasterisation group in tile rows (0 = default)
     fixup: str = "owner"    # "owner" (owner waits for peers), "last_arriver" or "split"
     f32_kernel: str = "auto"   # FP32 problems: "auto", "ffma" or "tf32x3"
+    coverage: int = 0       # device pointer of a coverage-count buffer (see coverage_counts)
 
     def to_c(self) -> B.sk_config:
         c = B.sk_config()
@@ -48,6 +49,7 @@ class Config:
         c.fixup = B.FIXUP_NAMES[self.fixup] if isinstance(self.fixup, str) else int(self.fixup)
         c.f32_kernel = (B.F32_KERNEL_NAMES[self.f32_kernel] if isinstance(self.f32_kernel, str)
                         else int(self.f32_kernel))
+        c.coverage = self.coverage or None
         return c
 
 
@@ -342,3 +344,33 @@ def trace_gemm(A: torch.Tensor, Bm: torch.Tensor, out: torch.Tensor | None = Non
         per.append(evs)
     per = [[(n, i, t - t0) for (n, i, t) in evs] for evs in per]
     return C, per
+
+
+def coverage_counts(As, Bs, outs=None, config=None, **kw):
+    """Run one GEMM (``As``, ``Bs`` tensors) or one grouped GEMM (lists) with
+    the kernel's coverage counting on.  Returns (outputs, words, plan) with
+    ``words`` the SK_COVERAGE words as a host int64 tensor: the first
+    ``total_iters`` count the MAC-loop iterations, the rest the 32 x 32
+    blocks of C each unit stored (layout in include/skgemm.h)."""
+    import dataclasses
+    cfg = config or Config()
+    grouped = isinstance(As, (list, tuple))
+    A_list, B_list = (list(As), list(Bs)) if grouped else ([As], [Bs])
+    if outs is None:
+        out_dtype = kw.pop("out_dtype", None)
+        outs = [torch.empty((a.shape[0], b.shape[1]),
+                            dtype=out_dtype or (torch.float32 if a.dtype == torch.float32 else torch.bfloat16),
+                            device=a.device) for a, b in zip(A_list, B_list)]
+    elif not grouped:
+        outs = [outs]
+    probs = [make_problem(a, b, c) for a, b, c in zip(A_list, B_list, outs)]
+    info = plan(probs, cfg)
+    buf = torch.zeros(max(1, info.coverage_words), dtype=torch.int32, device=A_list[0].device)
+    cfg = dataclasses.replace(cfg, coverage=buf.data_ptr())
+    if grouped:
+        grouped_gemm(A_list, B_list, outs, config=cfg, **kw)
+    else:
+        gemm(A_list[0], B_list[0], outs[0], config=cfg, **kw)
+    torch.cuda.synchronize()
+    words = buf[:info.coverage_words].cpu().to(torch.int64) & 0xFFFFFFFF
+    return (outs if grouped else outs[0]), words, info

@@ -50,7 +50,7 @@ class sk_config(ctypes.Structure):
         ("mode", ctypes.c_int), ("num_ctas", ctypes.c_int),
         ("min_iters_per_unit", ctypes.c_int), ("timeout_ns", ctypes.c_uint64),
         ("debug_flags", ctypes.c_int), ("trace", ctypes.c_void_p), ("raster_group", ctypes.c_int),
-        ("fixup", ctypes.c_int), ("f32_kernel", ctypes.c_int),
+        ("fixup", ctypes.c_int), ("f32_kernel", ctypes.c_int), ("coverage", ctypes.c_void_p),
     ]
 
 SK_F32_AUTO, SK_F32_FFMA, SK_F32_TF32X3 = 0, 1, 2
@@ -62,7 +62,7 @@ FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER, "
 SK_TRACE_ENTRIES = 128
 SK_TRACE_BYTES_PER_CTA = SK_TRACE_ENTRIES * 16
 TRACE_EVENTS = {1: "start", 2: "mma_begin", 4: "mma_end", 5: "epi_begin",
-                6: "epi_flags", 7: "epi_end", 8: "end", 11: "fix_issue", 12: "fix_first_data",
+                6: "epi_flags", 7: "epi_end", 8: "end", 9: "entry", 11: "fix_issue", 12: "fix_first_data",
                 13: "fix_last_data", 14: "spill_issued", 15: "spill_visible",
                 16: "split_summed"}
 
@@ -76,6 +76,7 @@ class sk_plan_info(ctypes.Structure):
         ("sk_iters", ctypes.c_int64), ("iters_per_unit", ctypes.c_int64),
         ("extra_units", ctypes.c_int64), ("workspace_bytes", ctypes.c_size_t),
         ("predicted_us", ctypes.c_double), ("fixup", ctypes.c_int),
+        ("coverage_words", ctypes.c_int64),
     ]
 
 

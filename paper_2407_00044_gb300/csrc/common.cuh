@@ -112,12 +112,18 @@ struct TcParams {
   int32_t stages;
   int32_t debug_flags;
   uint64_t *trace;      // optional per-CTA timeline (SK_TRACE_* in skgemm.h)
+  uint32_t *cover;      // optional coverage counts (SK_COVERAGE in skgemm.h)
+  int64_t cover_iters;  // MAC-loop iterations of all problems: the first block-store word
   int32_t fixup;
   int32_t pad_;
 };
 
+// Coverage word increment of one visit by unit u (SK_COVERAGE_VISIT).
+__host__ __device__ __forceinline__ uint32_t cover_visit(int u) { return 1u + ((uint32_t)(u + 1) << 8); }
+
 constexpr int TRACE_ENTRIES = 128;
-constexpr int TRACE_MMA_BASE = 0, TRACE_EPI_BASE = 48, TRACE_CTA_BASE = 112, TRACE_FIX_BASE = 116;
+constexpr int TRACE_MMA_BASE = 0, TRACE_EPI_BASE = 48, TRACE_CTA_BASE = 112, TRACE_FIX_BASE = 116,
+              TRACE_ENTRY = 122;
 
 __device__ __forceinline__ void trace_put(uint64_t *trace, int entry, uint32_t ev, uint32_t item, uint64_t t) {
   if (trace && entry >= 0 && entry < TRACE_ENTRIES) {

@@ -136,7 +136,7 @@ struct OutStore<__nv_bfloat16> {
 //   on both CTAs' barriers (multicast).  Each CTA's epilogue handles its own
 //   128 rows; both CTAs' epilogues release the leader's `tmem_empty`.  Each
 //   CTA of a pair has its own partial slot and flag (index 2*unit + rank).
-template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool TRACE>
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG>
 __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ TcParams<MAXP> P) {
   using Tr = InTraits<IN>;
   constexpr int BM = PAIR ? 256 : 128;          // tile rows per unit
@@ -197,6 +197,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   const TcProblem *const probs = gtab ? P.gprob : P.prob;
   const ProbSched *const pss = gtab ? P.gps : P.ps;
 
+  // (debug variant) the moment this CTA entered the kernel, before any set-up
+  if (DBG && threadIdx.x == 0) trace_put(P.trace, TRACE_ENTRY, 9, 0, globaltimer_ordered());
   if (threadIdx.x == 0) {
     for (int s = 0; s < stages; ++s) {
       mbar_init(smem_u32(full_bar + s), 1);
@@ -229,9 +231,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   if constexpr (PAIR) cluster_sync();   // the peer's barriers exist before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  // Timeline tracing is compiled only into the TRACE instantiations.
-  uint64_t *const trace = TRACE ? P.trace : nullptr;
-  if (TRACE && threadIdx.x == 0) trace_put(trace, TRACE_CTA_BASE, 1, 0, globaltimer_ordered());
+  // Timeline tracing and coverage counting are compiled only into the DBG
+  // instantiations (launched when a trace or coverage buffer is given).
+  uint64_t *const trace = DBG ? P.trace : nullptr;
+  uint32_t *const cover = DBG ? P.cover : nullptr;
+  if (DBG && threadIdx.x == 0) trace_put(trace, TRACE_CTA_BASE, 1, 0, globaltimer_ordered());
 
   auto fail = [&]() {
     *abort_flag = 1;
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           break;
         }
         tc_fence_after();
-        if (TRACE && nitem < 16) trace_put(trace, tr, 2, nitem, globaltimer());
+        if (DBG && nitem < 16) trace_put(trace, tr, 2, nitem, globaltimer());
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
         for (int kb = w.k0; kb < w.k1; ++kb) {
           // 3xTF32 waits for the epilogue warps' conversion of the stage
@@ -432,6 +436,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             mma_commit_pair_mc(smem_u32(empty_bar + stage), (uint16_t)3);
           else
             mma_commit(smem_u32(empty_bar + stage));
+          if (DBG && cover) {
+            // this unit issued MAC-loop iteration (tile, kb)
+            const ProbSched &q = pss[w.problem];
+            atomicAdd(cover + q.iter_base + (int64_t)w.tile * q.iters + kb, cover_visit(u));
+          }
           if (++stage == stages) {
             stage = 0;
             phase ^= 1u;
@@ -442,7 +451,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           mma_commit_pair_mc(smem_u32(tfull_bar + acc), (uint16_t)3);
         else
           mma_commit(smem_u32(tfull_bar + acc));
-        if (TRACE && nitem < 16) trace_put(trace, tr + 2, 4, nitem, globaltimer());
+        if (DBG && nitem < 16) trace_put(trace, tr + 2, 4, nitem, globaltimer());
         ++nitem;
         if (++acc == 2) {
           acc = 0;
@@ -491,7 +500,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     // Slot / flag / counter index of unit p's CTA holding these rows.
     auto cslot = [&](int p) { return PAIR ? 2 * p + (int)rank : p; };
     int nitem = 0;
-    const bool tr_lead = TRACE && et == 0;
+    const bool tr_lead = DBG && et == 0;
     // Loop exit and wait results are made uniform over the 128 epilogue
     // threads: the lanes of a warp must stay converged for the
     // warp-collective tcgen05.ld, and all four warps must reach the same
@@ -564,6 +573,12 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       const int grow = w.tm * BM + (int)rank * 128 + row;
       const int row0 = w.tm * BM + (int)rank * 128 + q4 * 32;   // first row of this warp
       auto store_chunk = [&](int ch, const float (&v)[32], float alpha) {
+        if (DBG && cover && lane == 0) {
+          // this unit stores the 32 x 32 block (rows of this warp, chunk ch)
+          constexpr int BLK_N = BN / 32;
+          const int64_t blk = w.gtile * (int64_t)(BM / 32) * BLK_N + ((int)rank * 4 + q4) * BLK_N + ch;
+          atomicAdd(cover + P.cover_iters + blk, cover_visit(u));
+        }
         if (pr.c_tma) {
           // Stage the chunk in shared memory and write it with one TMA
           // store per 128-byte-wide box (BF16: 64 columns = two chunks;
@@ -1042,7 +1057,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   // stamps when its role is done; the CTA ends at the latest of these.
   // (A stamp taken right after a barrier can be read before the barrier
   // completes, so none is taken there.)
-  if (TRACE) {
+  if (DBG) {
     const int role_lead = threadIdx.x == 0 ? 0 : threadIdx.x == 32 ? 1 : threadIdx.x == 64 ? 2 : -1;
     if (role_lead >= 0) trace_put(trace, TRACE_CTA_BASE + 1 + role_lead, 8, role_lead, globaltimer_ordered());
   }
@@ -1059,9 +1074,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   }
 }
 
-template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool TRACE>
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG>
 cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, TRACE>;
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, DBG>;
   const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages, IN == IN_TF32X3);
   (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1088,12 +1103,19 @@ cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st
   }
 }
 
-// Tracing variants exist for single-problem BF16 and 3xTF32 launches;
-// elsewhere a trace buffer is ignored.
+// Debug variants (timeline trace, coverage counts) exist for single-problem
+// BF16 and 3xTF32 launches and for grouped BF16 launches with BF16 output;
+// elsewhere both buffers are ignored.
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
+constexpr bool has_debug_variant() {
+  return (IN == IN_BF16 && (MAXP == 1 || std::is_same<OutT, __nv_bfloat16>::value)) ||
+         (IN == IN_TF32X3 && MAXP == 1);
+}
+
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
 cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  if constexpr ((IN == IN_BF16 || IN == IN_TF32X3) && MAXP == 1) {
-    if (p.trace) return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true>(p, grid, st);
+  if constexpr (has_debug_variant<IN, OutT, BN, MAXP, PAIR>()) {
+    if (p.trace || p.cover) return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true>(p, grid, st);
   }
   return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, false>(p, grid, st);
 }

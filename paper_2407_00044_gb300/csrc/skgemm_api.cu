@@ -191,6 +191,7 @@ struct Cfg {
   uint64_t timeout_ns;
   int debug_flags;
   uint64_t *trace;
+  uint32_t *cover;
   int raster_group;
   int fixup;       // FIXUP_OWNER, FIXUP_LAST_ARRIVER or FIXUP_SPLIT
   bool tc32 = false;   // FP32 on the tensor cores (3xTF32) instead of FFMA
@@ -249,6 +250,7 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.timeout_ns = d.timeout_ns ? d.timeout_ns : 2000000000ull;
   r.debug_flags = d.debug_flags;
   r.trace = d.trace;
+  r.cover = d.coverage;
   if (d.raster_group < 0 || d.raster_group > 64) return SK_ERR_INVALID_ARG;
   r.raster_group = d.raster_group ? d.raster_group : GROUP_M_DEFAULT;
   if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER && d.fixup != SK_FIXUP_SPLIT)
@@ -300,6 +302,13 @@ struct PlanOut {
   int grid;
   double predicted_ns = 0;
 };
+
+// MAC-loop iterations (k-blocks of every tile) of all problems of a plan.
+int64_t total_iters(const PlanOut &pl) {
+  if (pl.ps.empty()) return 0;
+  const ProbSched &q = pl.ps.back();
+  return q.iter_base + (int64_t)q.tiles_m * q.tiles_n * q.iters;
+}
 
 int64_t count_sk_tiles(int64_t T, int64_t g, sk_mode mode) {
   switch (mode) {
@@ -753,6 +762,8 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   P->stages = c.stages;
   P->debug_flags = c.debug_flags;
   P->trace = c.trace;
+  P->cover = c.cover;
+  P->cover_iters = total_iters(pl);
   P->fixup = c.fixup;
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
@@ -1351,6 +1362,7 @@ sk_status sk_plan_query(const sk_problem *problems, int count, const sk_config *
   out->predicted_us = pl.predicted_ns * 1e-3;
   out->fixup = c.fixup == FIXUP_SPLIT ? SK_FIXUP_SPLIT : c.fixup == FIXUP_LAST_ARRIVER ? SK_FIXUP_LAST_ARRIVER
                                                                                          : SK_FIXUP_OWNER;
+  out->coverage_words = total_iters(pl) + pl.s.total_tiles * (int64_t)(c.BM / 32) * (c.BN / 32);
   return SK_OK;
 }
 

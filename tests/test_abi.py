@@ -464,3 +464,19 @@ def test_workspace_size_large_groups(sk):
     assert base < n.value < s256
     big = (B.sk_problem * 65537)()
     assert B.sk_workspace_size(big, 65537, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_INVALID_ARG
+
+
+def test_coverage_words(sk):
+    """sk_plan_info.coverage_words: one word per MAC-loop iteration of every
+    tile of every problem, then one per 32 x 32 block of every tile."""
+    B = sk.binding
+    shapes = [(300, 520, 700), (1024, 256, 256), (64, 1000, 1500)]
+    for cfg in ({"tile_m": 128, "tile_n": 128}, {"tile_m": 128, "tile_n": 256}, {"tile_m": 256, "tile_n": 256}):
+        probs = [sk.shape_problem(*s) for s in shapes]
+        info = sk.plan(probs, cfg, num_sms=152)
+        BM, BN, BK = info.tile_m, info.tile_n, info.tile_k
+        tiles = [sch.tile_grid(M, N, BM, BN) for (M, N, K) in shapes]
+        iters = sum(tm * tn * -(-K // BK) for (tm, tn), (M, N, K) in zip(tiles, shapes))
+        ntiles = sum(tm * tn for tm, tn in tiles)
+        assert info.coverage_words == iters + ntiles * (BM // 32) * (BN // 32)
+    assert B.sk_config().coverage is None   # NULL by default: the normal kernels run

@@ -216,7 +216,7 @@ def test_trace_timeline(m):
         assert len(active) >= 2
         for evs in active:
             names = [n for n, _, _ in evs]
-            assert names[0] == "start"
+            assert names[:2] == ["entry", "start"]
             assert sorted(i for n, i, _ in evs if n == "end") == [0, 1, 2]   # every role reported
             t_end = max(t for n, _, t in evs if n == "end")
             assert all(t <= t_end for _, _, t in evs)
