@@ -820,9 +820,13 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         // test-only injection: peers never count their arrival, so every
         // other contributor's bounded wait expires
         const bool withhold = (P.debug_flags & DEBUG_SKIP_PEER_FLAG) && w.role == ROLE_PEER;
+        // Departures are counted per warp in the counter's high half (4 kc
+        // of them per tile); the last resets the counter for the next call.
+        const uint32_t last_depart = (uint32_t)(4 * kc - 1);
         if (s0 == s1) {
-          // nothing to sum here: arrive and depart at once
-          if (et == 0 && !withhold && (atom_add_acq_rel_gpu(cnt, 1u + SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1))
+          // nothing to sum here: arrive and depart (all four warps) at once
+          if (et == 0 && !withhold &&
+              (atom_add_acq_rel_gpu(cnt, 1u + 4 * SPLIT_DEPART) >> 16) == last_depart - 3u)
             *cnt = 0u;
         } else {
           if (et == 0) {
@@ -838,6 +842,18 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           }
           named_bar_sync(1, 128);
+          // A warp departs as soon as it no longer reads the other
+          // contributors' partials (its staged copies have landed), so the
+          // atomic's round trip overlaps its sum.  Relaxed: within this
+          // launch no slot of the tile is written again, and every warp
+          // departs only after its CTA has seen all arrivals.
+          uint32_t dep = 0;
+          bool departed = false;
+          auto depart = [&]() {
+            if (lane == 0) dep = atom_add_relaxed_gpu(cnt, SPLIT_DEPART);
+            departed = true;
+          };
+          if (nunit_w == 0) depart();
           if (nunit_w > 0) {
             const float alpha = get_alpha();
             // Adds this CTA's own partial of chunk ch (term jx of the sum)
@@ -918,6 +934,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                   okw = false;
                   break;
                 }
+                if (g0 + gn >= npieces) depart();   // every partial this warp needs is staged
                 if (tr_lead && group == 0) trace_put(trace, TRACE_FIX_BASE + 2, 13, nitem, globaltimer_ordered());
                 for (int bi = 0; bi < gn; ++bi) {
                   const int ch = chunk_of(kq);
@@ -949,8 +966,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             release_acc(acc);
           }
           if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 3, 16, nitem, globaltimer_ordered());
-          named_bar_sync(1, 128);   // every thread has read the partials
-          if (et == 0 && (atom_add_acq_rel_gpu(cnt, SPLIT_DEPART) >> 16) == (uint32_t)(kc - 1)) *cnt = 0u;
+          if (!departed) depart();   // plain-load sum done, or a staging wait failed
+          if (lane == 0 && (dep >> 16) == last_depart) *cnt = 0u;
         }
         if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       } else if (w.role == ROLE_PEER) {

@@ -120,11 +120,15 @@ def test_last_arriver_exactly_one_reducer(npeers):
 
 # ---- split reduce --------------------------------------------------------
 # Every contributor of a split tile spills its partial, counts its arrival in
-# the low 16 bits of the tile's counter, waits until all kc contributors have
-# arrived, sums its own share of the tile's columns from all kc partials (in
-# unit order), then counts its departure in the high bits; the last to depart
-# resets the counter.  A contributor with an empty share arrives and departs
-# in one atomic add.  Checked here over every interleaving of the steps.
+# the low 16 bits of the tile's counter and waits until all kc contributors
+# have arrived.  Then each of its W epilogue warps stages the partials of its
+# share of the tile's columns (reads the other contributors' slots), counts
+# its own departure in the high bits -- before it sums, so the atomic's round
+# trip overlaps the sum -- and sums from the staged copies.  The last of the
+# kc * W departures resets the counter.  A warp with an empty share departs
+# right after the wait; a contributor with an empty share arrives and departs
+# (all W warps) in one atomic add.  Checked here over every interleaving of
+# the steps of the contributors and of their warps.
 
 DEPART = 1 << 16
 
@@ -144,59 +148,77 @@ def test_split_shares_partition_the_tile(nu, kc):
     assert cols == list(range(nu))
 
 
-def _split_explore(kc, empty):
-    """DFS over all interleavings; each contributor is a program counter
-    over its steps.  Returns the number of terminal states reached."""
-    steps = {j: (["spill", "arrive_depart"] if j in empty else ["spill", "arrive", "wait", "sum", "depart"])
-             for j in range(kc)}
-    terminals = 0
+def _split_explore(kc, empty, warps=2, idle=()):
+    """Search over all interleavings.  Processes: each contributor's head
+    (spill, arrive, wait; or one arrive-and-depart if its share is empty)
+    and, once the head has waited, each of its warps (stage, depart; or only
+    depart for the (contributor, warp) pairs in `idle`).  Returns the number
+    of distinct terminal states."""
+    procs = []
+    for j in range(kc):
+        if j in empty:
+            procs.append((j, None, ["spill", "arrive_depart"]))
+        else:
+            procs.append((j, None, ["spill", "arrive", "wait"]))
+            for w in range(warps):
+                procs.append((j, w, ["depart"] if (j, w) in idle else ["stage", "depart"]))
+    head = {j: i for i, (j, w, _) in enumerate(procs) if w is None}
+    last = kc * warps - 1
+    terminals = set()
+    seen = set()
 
-    def go(pc, counter, written, summed):
-        nonlocal terminals
+    def go(pc, counter, written, staged):
+        key = (pc, counter, written, staged)
+        if key in seen:
+            return
+        seen.add(key)
         moved = False
-        for j in range(kc):
-            if pc[j] == len(steps[j]):
+        for i, (j, w, steps) in enumerate(procs):
+            if pc[i] == len(steps):
                 continue
-            s = steps[j][pc[j]]
-            c2, w2, s2 = counter, written, summed
+            if w is not None and pc[head[j]] < 3:
+                continue                     # the warps start after their CTA's wait
+            s = steps[pc[i]]
+            c2, w2, s2 = counter, written, staged
             if s == "spill":
                 w2 = written | {j}
             elif s == "arrive":
                 c2 = counter + 1
             elif s == "arrive_depart":
-                old = counter
-                c2 = counter + 1 + DEPART
-                if (old >> 16) == kc - 1:
+                c2 = counter + 1 + warps * DEPART
+                if (counter >> 16) == last - (warps - 1):
                     c2 = 0
             elif s == "wait":
                 if (counter & 0xFFFF) < kc:
-                    continue                 # blocked: no move for j
-            elif s == "sum":
-                # every partial it reads must be written
+                    continue                 # blocked: no move
+            elif s == "stage":
+                # every partial the warp reads must be written
                 assert written == set(range(kc))
-                s2 = summed | {j}
+                s2 = staged | {(j, w)}
             elif s == "depart":
-                old = counter
                 c2 = counter + DEPART
-                if (old >> 16) == kc - 1:
-                    assert summed == set(range(kc)) - set(empty)
+                if (counter >> 16) == last:
+                    # nobody reads a slot of the tile any more
+                    need = {(jj, ww) for jj in range(kc) if jj not in empty
+                            for ww in range(warps) if (jj, ww) not in idle}
+                    assert staged == need
                     c2 = 0
             moved = True
-            go(pc[:j] + (pc[j] + 1,) + pc[j + 1:], c2, w2, s2)
+            go(pc[:i] + (pc[i] + 1,) + pc[i + 1:], c2, w2, s2)
         if not moved:
-            # no contributor can move: all must be finished (no deadlock)
-            assert all(pc[j] == len(steps[j]) for j in range(kc)), (pc, counter)
+            # no process can move: all must be finished (no deadlock)
+            assert all(pc[i] == len(steps) for i, (_, _, steps) in enumerate(procs)), (pc, counter)
             assert counter == 0
-            assert summed == set(range(kc)) - set(empty)
-            terminals += 1
+            terminals.add(key)
 
-    go(tuple([0] * kc), 0, frozenset(), frozenset())
-    return terminals
+    go(tuple([0] * len(procs)), 0, frozenset(), frozenset())
+    return len(terminals)
 
 
-@pytest.mark.parametrize("kc,empty", [(2, ()), (3, ()), (3, (1,)), (4, (0, 2)), (3, (0, 1))])
-def test_split_reduce_every_interleaving(kc, empty):
-    assert _split_explore(kc, empty) > 0
+@pytest.mark.parametrize("kc,empty,idle", [(2, (), ()), (3, (), ()), (3, (1,), ()), (4, (0, 2), ()),
+                                           (3, (0, 1), ()), (2, (), ((1, 0),)), (3, (2,), ((0, 1),))])
+def test_split_reduce_every_interleaving(kc, empty, idle):
+    assert _split_explore(kc, empty, idle=idle) > 0
 
 
 @pytest.mark.parametrize("bn,f32_out", [(128, True), (128, False), (256, True), (256, False)])
