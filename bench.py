@@ -287,7 +287,7 @@ def run_ours(args, world, rank, local):
         per_shape.append({
             "M": M, "N": N, "K": K,
             "tile": f"{info.tile_m}x{info.tile_n}", "mode": ["auto", "dp", "sk", "hybrid1", "hybrid2"][info.mode],
-            "units": info.num_ctas, "fixup": ["owner", "last_arriver", "split"][info.fixup],
+            "units": info.num_ctas, "fixup": ["owner", "last_arriver", "split", "split_cluster"][info.fixup],
             "ms": round(ms_sk, 4), "tflops": round(f / ms_sk / 1e9, 1),
             "pct_peak": round(100 * f / ms_sk / 1e9 / pk["bf16"], 1),
             "pct_hw": round(100 * f / ms_sk / 1e9 / hw_at_clock, 1),

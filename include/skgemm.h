@@ -109,9 +109,10 @@ typedef struct {
 } sk_problem;
 
 /* How a tile split across units gets its partial sums added (Stream-K's
- * "fixup", Background and Methodology sections).  Both orders of addition are
- * the same -- the partial of the unit holding k-block 0 first, then the other
- * units' partials by ascending unit index -- so both give bit-identical C. */
+ * "fixup", Background and Methodology sections).  Every protocol adds in the
+ * same order -- the partial of the unit holding k-block 0 first, then the
+ * other units' partials by ascending unit index -- so all give bit-identical
+ * C (with two partials the single addition is order-free). */
 typedef enum {
     SK_FIXUP_OWNER = 0,        /* the unit holding k-block 0 waits (bounded) for
                                   the others' flags and adds their partials */
@@ -120,7 +121,7 @@ typedef enum {
                                   completes the count adds all partials.  No unit
                                   ever waits; the workspace holds twice the partial
                                   slots (no counterpart in the paper) */
-    SK_FIXUP_SPLIT = 2         /* for plans where every unit holds one range inside
+    SK_FIXUP_SPLIT = 2,        /* for plans where every unit holds one range inside
                                   one tile (all Stream-K, equal ranges dividing the
                                   tiles' k-blocks; otherwise SK_ERR_UNSUPPORTED):
                                   every contributor spills and waits (bounded) for
@@ -130,6 +131,17 @@ typedef enum {
                                   count left to the library, the library uses it
                                   where its runtime model predicts a gain (no
                                   counterpart in the paper) */
+    SK_FIXUP_SPLIT_CLUSTER = 3 /* the split reduce for plans that cut every tile
+                                  into exactly two ranges (2 units per tile):
+                                  the tile's two units run as one thread-block
+                                  cluster (2 CTAs, or 2 CTA pairs) and each writes
+                                  the half of its partial that the other sums
+                                  straight into the other's shared memory -- no
+                                  workspace slots or flags.  Single-problem BF16
+                                  calls on 128-row tiles or 256 x 256 pairs, with
+                                  one co-resident cluster per tile; otherwise
+                                  SK_ERR_UNSUPPORTED.  Chosen by the library like
+                                  SK_FIXUP_SPLIT (no counterpart in the paper) */
 } sk_fixup;
 
 /* Kernel for FP32 problems. */

@@ -30,7 +30,7 @@ class Config:
     debug_flags: int = 0
     trace: int = 0          # device pointer of a timeline buffer (see trace_gemm)
     raster_group: int = 0   # rasterisation group in tile rows (0 = default)
-    fixup: str = "owner"    # "owner" (owner waits for peers), "last_arriver" or "split"
+    fixup: str = "owner"    # "owner" (owner waits for peers), "last_arriver", "split" or "split_cluster"
     f32_kernel: str = "auto"   # FP32 problems: "auto", "ffma" or "tf32x3"
     coverage: int = 0       # device pointer of a coverage-count buffer (see coverage_counts)
 

@@ -56,8 +56,9 @@ class sk_config(ctypes.Structure):
 SK_F32_AUTO, SK_F32_FFMA, SK_F32_TF32X3 = 0, 1, 2
 F32_KERNEL_NAMES = {"auto": SK_F32_AUTO, "ffma": SK_F32_FFMA, "tf32x3": SK_F32_TF32X3}
 
-SK_FIXUP_OWNER, SK_FIXUP_LAST_ARRIVER, SK_FIXUP_SPLIT = 0, 1, 2
-FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER, "split": SK_FIXUP_SPLIT}
+SK_FIXUP_OWNER, SK_FIXUP_LAST_ARRIVER, SK_FIXUP_SPLIT, SK_FIXUP_SPLIT_CLUSTER = 0, 1, 2, 3
+FIXUP_NAMES = {"owner": SK_FIXUP_OWNER, "last_arriver": SK_FIXUP_LAST_ARRIVER, "split": SK_FIXUP_SPLIT,
+               "split_cluster": SK_FIXUP_SPLIT_CLUSTER}
 
 SK_TRACE_ENTRIES = 128
 SK_TRACE_BYTES_PER_CTA = SK_TRACE_ENTRIES * 16

@@ -34,7 +34,7 @@ constexpr size_t WS_FLAG_OFFSET = 256;
 constexpr size_t WS_FLAG_BYTES = (size_t)WS_MAX_CTAS * 4;
 
 // Fixup protocols (sk_fixup).
-constexpr int32_t FIXUP_OWNER = 0, FIXUP_LAST_ARRIVER = 1, FIXUP_SPLIT = 2;
+constexpr int32_t FIXUP_OWNER = 0, FIXUP_LAST_ARRIVER = 1, FIXUP_SPLIT = 2, FIXUP_SPLIT_CLUSTER = 3;
 // Split reduce: one counter word per tile (at the owner's flag) counts
 // arrivals in its low half and departures in its high half.
 constexpr uint32_t SPLIT_DEPART = 1u << 16;
@@ -161,6 +161,11 @@ cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st);
 
 template <int IN, typename OutT, int BN, int MAXP>
 int pair_max_clusters(int stages);
+
+// Co-resident clusters of the cluster-split kernel (FIXUP_SPLIT_CLUSTER,
+// single-problem BF16): two units per cluster.
+template <typename OutT, int BN, bool PAIR>
+int xs_max_clusters(int stages);
 
 cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N,
                          float beta, int c_is_f32, cudaStream_t st);

@@ -136,7 +136,13 @@ struct OutStore<__nv_bfloat16> {
 //   on both CTAs' barriers (multicast).  Each CTA's epilogue handles its own
 //   128 rows; both CTAs' epilogues release the leader's `tmem_empty`.  Each
 //   CTA of a pair has its own partial slot and flag (index 2*unit + rank).
-template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG>
+// XS = true (split tiles of exactly two contributors, FIXUP_SPLIT_CLUSTER):
+//   a tile's two units run as one cluster -- two CTAs, or two CTA pairs
+//   (cluster ranks 0-1 and 2-3, each pair its own cta_group::2 pair) -- and
+//   each CTA writes the half of its accumulator rows that the other sums
+//   straight into that CTA's shared memory (st.async, counted on its
+//   mbarrier): no workspace, no flags.
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG, bool XS>
 __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ TcParams<MAXP> P) {
   using Tr = InTraits<IN>;
   constexpr int BM = PAIR ? 256 : 128;          // tile rows per unit
@@ -177,7 +183,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *done_bar = tempty_bar + 2;
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
   uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage split (one per stage; the leader's in a pair)
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(conv_bar + (X3 ? stages : 0));
+  uint64_t *xr_bar = conv_bar + (X3 ? stages : 0);   // XS: the partner's ring is free to write
+  uint64_t *xd_bar = xr_bar + 1;                      // XS: the partner's half has arrived
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + 1);
   volatile uint32_t *abort_flag = tmem_slot + 1;
   volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
   volatile uint32_t *fix_fail = tmem_slot + 4;   // two words: a staged-sum group failed
@@ -185,7 +193,11 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+  // CTAs per cluster: a pair (2), or, XS, two units (4 CTAs or 2)
+  constexpr int CL = XS ? (PAIR ? 4 : 2) : (PAIR ? 2 : 1);
+  const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
+  const uint32_t rank = PAIR ? (XS ? (crank & 1u) : crank) : 0u;   // this CTA within its pair
+  const uint32_t pbase = (PAIR && XS) ? (crank & ~1u) : 0u;        // cluster rank of its pair's leader
   const bool leader = rank == 0;
   const int u = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int slot_id = PAIR ? 2 * u + (int)rank : u;   // workspace slot / flag of this CTA
@@ -210,6 +222,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     }
     mbar_init(smem_u32(done_bar), 1);
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
+    if constexpr (XS) {
+      mbar_init(smem_u32(xr_bar), 1);   // the partner's one remote arrival
+      mbar_init(smem_u32(xd_bar), 1);   // this CTA's arrive.expect_tx
+    }
     if constexpr (X3)   // the 4 epilogue warps of this CTA (of both CTAs in a pair)
       for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), PAIR ? 8 : 4);
     *abort_flag = 0;
@@ -228,7 +244,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   }
   tc_fence_before();
   cta_sync();
-  if constexpr (PAIR) cluster_sync();   // the peer's barriers exist before anyone signals them
+  if constexpr (CL > 1) cluster_sync();   // the other CTAs' barriers exist before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Timeline tracing and coverage counting are compiled only into the DBG
@@ -284,7 +300,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           const uint32_t sb = sa + A_BYTES;
           const int kx = kb * BK;
           if constexpr (!OWN_FULL) {
-            const uint32_t fbl = mapa_shared(fb, 0);   // the leader's barrier
+            const uint32_t fbl = mapa_shared(fb, pbase);   // the leader's barrier
             if (kmaj) {
               tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
               tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
@@ -433,7 +449,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             }
           }
           if constexpr (PAIR)
-            mma_commit_pair_mc(smem_u32(empty_bar + stage), (uint16_t)3);
+            mma_commit_pair_mc(smem_u32(empty_bar + stage), (uint16_t)(3u << pbase));
           else
             mma_commit(smem_u32(empty_bar + stage));
           if (DBG && cover) {
@@ -448,7 +464,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         }
         if (!ok) break;
         if constexpr (PAIR)
-          mma_commit_pair_mc(smem_u32(tfull_bar + acc), (uint16_t)3);
+          mma_commit_pair_mc(smem_u32(tfull_bar + acc), (uint16_t)(3u << pbase));
         else
           mma_commit(smem_u32(tfull_bar + acc));
         if (DBG && nitem < 16) trace_put(trace, tr + 2, 4, nitem, globaltimer());
@@ -461,7 +477,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       if (!ok) fail();
       // All MMAs issued by this thread are complete once done_bar flips.
       if constexpr (PAIR)
-        mma_commit_pair_mc(smem_u32(done_bar), (uint16_t)1);
+        mma_commit_pair_mc(smem_u32(done_bar), (uint16_t)(1u << pbase));
       else
         mma_commit(smem_u32(done_bar));
       if (!mbar_wait(smem_u32(done_bar), 0u, tmo)) fail();
@@ -492,7 +508,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       __syncwarp();
       if (lane == 0) {
         if constexpr (PAIR)
-          mbar_arrive_cluster(mapa_shared(smem_u32(tempty_bar + a), 0));
+          mbar_arrive_cluster(mapa_shared(smem_u32(tempty_bar + a), pbase));
         else
           mbar_arrive(smem_u32(tempty_bar + a));
       }
@@ -539,7 +555,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           __syncwarp();
           if (lane == 0) {
             if constexpr (PAIR)   // the leader's MMAs read both CTAs' halves
-              mbar_arrive_cluster(mapa_shared(smem_u32(conv_bar + cstage), 0));
+              mbar_arrive_cluster(mapa_shared(smem_u32(conv_bar + cstage), pbase));
             else
               mbar_arrive(smem_u32(conv_bar + cstage));
           }
@@ -783,7 +799,72 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       // partials, the first from TMEM (own_tmem) or from o's owner slot.
       bool do_sum = false, own_tmem = true;
       int o = u, pl = w.peer_last;
-      if (split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+      if (XS && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+        // Cluster split (the host launches it only when every tile has
+        // exactly two contributors, the owner jx = 0 and its peer jx = 1,
+        // and they are the cluster's two units).  Contributor jx sums
+        // columns [jx BN/2, (jx+1) BN/2) of its 128 rows: it writes the
+        // other half of its accumulator into the partner CTA's operand ring
+        // (free once the partner's MMAs are done, which the partner
+        // signals) in TMEM-fragment order, 16 KB per 32-column chunk, and
+        // receives its own half's other partial the same way.  C = alpha
+        // (P0 + P1): one addition, so the result is bit-identical to the
+        // other protocols whichever term comes first.
+        constexpr int HCH = BN / 64;                       // 32-column chunks per half
+        const int jx = w.role == ROLE_OWNER ? 0 : 1;
+        const int own_c0 = jx * HCH, oth_c0 = (1 - jx) * HCH;
+        const uint32_t partner = crank ^ (PAIR ? 2u : 1u);
+        if (et == 0) {
+          mbar_arrive_expect_tx(smem_u32(xd_bar), (uint32_t)(HCH * 16384));
+          mbar_arrive_cluster(mapa_shared(smem_u32(xr_bar), partner));   // this ring is free
+        }
+        // (cluster-scope acquires: the arrival and the data come from the partner)
+        bool okx = mbar_wait_cluster(smem_u32(xr_bar), 0u, tmo);
+        if (named_bar_or(1, 128, !okx)) {
+          if (et == 0) fail();
+        } else {
+          const uint32_t rring = mapa_shared(tiles_addr, partner);
+          const uint32_t rbar = mapa_shared(smem_u32(xd_bar), partner);
+#pragma unroll 1
+          for (int c = 0; c < HCH; c += 2) {
+            float v[64];
+            tmem_ld64(tbase + (oth_c0 + c) * 32, v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                st_async_v4(rring + (uint32_t)(((((c + h) * 4 + q4) * 8 + j) * 32 + lane) * 16),
+                            make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2],
+                                        v[32 * h + 4 * j + 3]),
+                            rbar);
+          }
+          if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // half sent
+          okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar), 0u, tmo));
+          if (!okx && lane == 0) fail();
+          if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
+          const float alpha = get_alpha();
+          const float4 *rx = reinterpret_cast<const float4 *>(smem);
+#pragma unroll 1
+          for (int c = 0; c < HCH; c += 2) {
+            float v[64];
+            tmem_ld64(tbase + (own_c0 + c) * 32, v);
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 q = rx[(((c + h) * 4 + q4) * 8 + j) * 32 + lane];
+                v[32 * h + 4 * j] += q.x;
+                v[32 * h + 4 * j + 1] += q.y;
+                v[32 * h + 4 * j + 2] += q.z;
+                v[32 * h + 4 * j + 3] += q.w;
+              }
+            store_chunk(own_c0 + c, *reinterpret_cast<const float(*)[32]>(v), alpha);
+            store_chunk(own_c0 + c + 1, *reinterpret_cast<const float(*)[32]>(v + 32), alpha);
+          }
+        }
+        release_acc(acc);
+        if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
+      } else if (split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
         // Split reduce (the host uses it only when every unit holds one
         // tile-aligned range, so a tile's units finish together): every
         // contributor spills what the others sum, counts its arrival, waits
@@ -1054,7 +1135,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             P.ws.flags[cslot(o)] = 0u;
         }
       }
-      if (!(split_reduce && (w.role == ROLE_PEER || w.role == ROLE_OWNER))) {
+      if (!((XS || split_reduce) && (w.role == ROLE_PEER || w.role == ROLE_OWNER))) {
         if (w.role != ROLE_PEER) release_acc(acc);
         if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       }
@@ -1079,9 +1160,10 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     if (role_lead >= 0) trace_put(trace, TRACE_CTA_BASE + 1 + role_lead, 8, role_lead, globaltimer_ordered());
   }
   cta_sync();
-  // A pair's leader MMAs read the peer's shared memory and write its TMEM:
-  // neither CTA frees TMEM or exits before both are done.
-  if constexpr (PAIR) cluster_sync();
+  // A pair's leader MMAs read the peer's shared memory and write its TMEM,
+  // and XS partners write each other's shared memory: no CTA of a cluster
+  // frees TMEM or exits before all are done.
+  if constexpr (CL > 1) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     if constexpr (PAIR)
@@ -1091,14 +1173,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   }
 }
 
-template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG>
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG, bool XS>
 cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, DBG>;
+  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, DBG, XS>;
+  constexpr int CL = XS ? (PAIR ? 4 : 2) : (PAIR ? 2 : 1);
   const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages, IN == IN_TF32X3);
   (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if constexpr (!PAIR) {
+  if constexpr (CL == 1) {
     kern<<<grid, 192, smem, st>>>(p);
     return cudaGetLastError();
   } else {
@@ -1111,7 +1194,7 @@ cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -1129,27 +1212,47 @@ constexpr bool has_debug_variant() {
          (IN == IN_TF32X3 && MAXP == 1);
 }
 
+// Cluster-split variants (FIXUP_SPLIT_CLUSTER) exist for single-problem
+// BF16 launches on 128 x 128 / 128 x 256 tiles and 256 x 256 pairs.
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
-cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
-  if constexpr (has_debug_variant<IN, OutT, BN, MAXP, PAIR>()) {
-    if (p.trace || p.cover) return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true>(p, grid, st);
-  }
-  return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, false>(p, grid, st);
+constexpr bool has_xs_variant() {
+  return IN == IN_BF16 && MAXP == 1 && (!PAIR || BN == 256);
 }
 
-// Co-resident clusters of two for the pair kernel (0 if it cannot launch).
-template <int IN, typename OutT, int BN, int MAXP>
-int pair_max_clusters(int stages) {
-  auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, true, false>;
-  const int smem = tc_smem_bytes(BN / 2, stages, IN == IN_TF32X3);
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
+cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
+  if constexpr (has_xs_variant<IN, OutT, BN, MAXP, PAIR>()) {
+    if (p.fixup == FIXUP_SPLIT_CLUSTER)
+      return (p.trace || p.cover) ? launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true, true>(p, grid, st)
+                                  : launch_tc_variant<IN, OutT, BN, MAXP, PAIR, false, true>(p, grid, st);
+  }
+  if (p.fixup == FIXUP_SPLIT_CLUSTER) return cudaErrorNotSupported;
+  if constexpr (has_debug_variant<IN, OutT, BN, MAXP, PAIR>()) {
+    if (p.trace || p.cover) return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, true, false>(p, grid, st);
+  }
+  return launch_tc_variant<IN, OutT, BN, MAXP, PAIR, false, false>(p, grid, st);
+}
+
+// Co-resident clusters of the kernel (0 if it cannot launch): CTA pairs
+// (xs = false), or, for the cluster split (xs = true), clusters of two
+// units -- four CTAs for pairs, two single CTAs otherwise.
+template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
+int tc_max_clusters(int stages, bool xs) {
+  constexpr bool XS_OK = has_xs_variant<IN, OutT, BN, MAXP, PAIR>();
+  if (xs && !XS_OK) return 0;
+  if (!xs && !PAIR) return 0;
+  auto kern = xs ? sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, false, XS_OK>
+                 : sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, false, false>;
+  const int cl = xs ? (PAIR ? 4 : 2) : 2;
+  const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, stages, IN == IN_TF32X3);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(2, 1, 1);
+  cfg.gridDim = dim3((unsigned)cl, 1, 1);
   cfg.blockDim = dim3(192, 1, 1);
   cfg.dynamicSmemBytes = (size_t)smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.x = (unsigned)cl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -1160,6 +1263,16 @@ int pair_max_clusters(int stages) {
     return 0;
   }
   return n;
+}
+
+template <int IN, typename OutT, int BN, int MAXP>
+int pair_max_clusters(int stages) {
+  return tc_max_clusters<IN, OutT, BN, MAXP, true>(stages, false);
+}
+
+template <typename OutT, int BN, bool PAIR>
+int xs_max_clusters(int stages) {
+  return tc_max_clusters<IN_BF16, OutT, BN, 1, PAIR>(stages, true);
 }
 
 }  // namespace sk

@@ -193,7 +193,7 @@ struct Cfg {
   uint64_t *trace;
   uint32_t *cover;
   int raster_group;
-  int fixup;       // FIXUP_OWNER, FIXUP_LAST_ARRIVER or FIXUP_SPLIT
+  int fixup;       // FIXUP_OWNER, FIXUP_LAST_ARRIVER, FIXUP_SPLIT or FIXUP_SPLIT_CLUSTER
   bool tc32 = false;   // FP32 on the tensor cores (3xTF32) instead of FFMA
   int ctas() const { return pair ? 2 * g : g; }
 };
@@ -253,10 +253,14 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   r.cover = d.coverage;
   if (d.raster_group < 0 || d.raster_group > 64) return SK_ERR_INVALID_ARG;
   r.raster_group = d.raster_group ? d.raster_group : GROUP_M_DEFAULT;
-  if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER && d.fixup != SK_FIXUP_SPLIT)
+  if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER && d.fixup != SK_FIXUP_SPLIT &&
+      d.fixup != SK_FIXUP_SPLIT_CLUSTER)
     return SK_ERR_INVALID_ARG;
+  // the cluster split: single-problem BF16 on 128-row tiles or 256 x 256 pairs
+  if (d.fixup == SK_FIXUP_SPLIT_CLUSTER && (fam != FAM_BF16 || (r.pair && r.BN != 256))) return SK_ERR_UNSUPPORTED;
   r.fixup = d.fixup == SK_FIXUP_LAST_ARRIVER ? FIXUP_LAST_ARRIVER
             : d.fixup == SK_FIXUP_SPLIT      ? FIXUP_SPLIT
+            : d.fixup == SK_FIXUP_SPLIT_CLUSTER ? FIXUP_SPLIT_CLUSTER
                                              : FIXUP_OWNER;
   *out = r;
   return SK_OK;
@@ -266,7 +270,8 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
 // region, and per CTA one partial slot (128 rows x BN FP32); the
 // last-arriver fixup adds a second slot per CTA.
 size_t ws_base_bytes(const Cfg &c) {
-  const size_t slots = (size_t)c.ctas() * 128 * c.BN * 4;
+  // (the cluster split exchanges partials between shared memories: no slots)
+  const size_t slots = c.fixup == FIXUP_SPLIT_CLUSTER ? 0 : (size_t)c.ctas() * 128 * c.BN * 4;
   return WS_FLAG_OFFSET + WS_FLAG_BYTES + (c.fixup == FIXUP_LAST_ARRIVER ? 2 : 1) * slots;
 }
 
@@ -445,6 +450,14 @@ bool split_eligible(const PlanOut &pl) {
   return true;
 }
 
+// The cluster split additionally needs one problem (the single-problem
+// kernels), every tile split into exactly two ranges (2 units per tile),
+// and a tile shape with a cluster-split kernel.
+bool xs_eligible(const PlanOut &pl, const Cfg &c) {
+  return pl.s.num_problems == 1 && c.fam == FAM_BF16 && (!c.pair || c.BN == 256) && split_eligible(pl) &&
+         (int64_t)pl.s.g == 2 * pl.s.total_tiles;
+}
+
 double algorithmic_dram_bytes(const std::vector<Norm> &work) {
   double b = 0;
   for (const Norm &n : work) {
@@ -532,6 +545,10 @@ double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const C
   return bytes;
 }
 
+// Cluster split: writing half an accumulator into the partner's shared
+// memory, as a fraction of a full spill to the workspace (estimate).
+constexpr double kXsExchangeFrac = 0.35;
+
 double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
   const ModelCoeffs k = model_coeffs(c);
   const Sched &s = pl.s;
@@ -568,7 +585,15 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
         const double mac_end = mac_start + (w.k1 - w.k0) * k.iter_ns * stretch + k.mac_item_ns;
         double start = std::max(mac_end, epi_prev);
         double e;
-        if (c.fixup == FIXUP_SPLIT && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+        if (c.fixup == FIXUP_SPLIT_CLUSTER && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
+          // the two contributors (units o, o + 1) each signal a free ring
+          // when their accumulator is complete, write the other's half
+          // into its shared memory and sum / store their own half
+          const int o = w.role == ROLE_OWNER ? u : u - 1;
+          spill_done[u] = start;
+          if (pass > 0) start = std::max(spill_done[o], spill_done[o + 1]);
+          e = kXsExchangeFrac * k.spill_ns + 0.5 * k.store_ns;
+        } else if (c.fixup == FIXUP_SPLIT && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
           // all contributors spill, wait for each other, then each reads
           // about one partial's bytes and stores its share of the tile
           int o = u, pl_ = w.peer_last;
@@ -874,8 +899,39 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
 // Fills the fields the caller left to the library (tile_m = 0, tile_n = 0,
 // mode = AUTO) with the candidate the runtime model predicts fastest.
 // Decisions are cached per problem set and config.
-sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vector<int> &idx, int sms,
-                      sk_config *d) {
+//
+// Co-resident clusters of the cluster-split kernel (two units each) for
+// config c on device `dev`, cached; with no device (dev < 0: plan queries
+// given an SM count) every SM is assumed usable.
+int xs_capacity(int dev, const Cfg &c, bool f32out, int sms) {
+  const int per = c.pair ? 4 : 2;
+  if (dev < 0 || dev >= 64) return sms / per;
+  static std::mutex mu;
+  static int cache[64][2][2][2][16] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  int &slot = cache[dev][c.pair ? 1 : 0][c.BN == 256 ? 1 : 0][f32out ? 1 : 0][c.stages & 15];
+  if (slot == 0) {
+    int n;
+    if (c.pair)
+      n = f32out ? xs_max_clusters<float, 256, true>(c.stages) : xs_max_clusters<__nv_bfloat16, 256, true>(c.stages);
+    else if (c.BN == 256)
+      n = f32out ? xs_max_clusters<float, 256, false>(c.stages) : xs_max_clusters<__nv_bfloat16, 256, false>(c.stages);
+    else
+      n = f32out ? xs_max_clusters<float, 128, false>(c.stages) : xs_max_clusters<__nv_bfloat16, 128, false>(c.stages);
+    slot = n > 0 ? n : -1;
+  }
+  return slot > 0 ? slot : 0;
+}
+
+// Whether plan `pl` of config `c` can run as a cluster split here: a
+// single-problem launch, eligible (xs_eligible), and one co-resident
+// cluster per tile.
+bool xs_runnable(const PlanOut &pl, const Cfg &c, const std::vector<Norm> &work, bool single, int dev, int sms) {
+  return single && xs_eligible(pl, c) && xs_capacity(dev, c, work[0].c_type == SK_F32, sms) >= pl.s.total_tiles;
+}
+
+sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vector<int> &idx, int sms, int dev,
+                      bool single, sk_config *d) {
   const bool free_tile_m = d->tile_m == 0;
   const bool free_tile_n = d->tile_n == 0 && fam != FAM_F32;
   const bool free_mode = d->mode == SK_MODE_AUTO;
@@ -889,9 +945,9 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
   std::string key;
   {
     char buf[160];
-    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n,
+    std::snprintf(buf, sizeof(buf), "%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|%d|", (int)fam, sms, d->tile_m, d->tile_n,
                   d->stages, (int)d->mode, d->num_ctas, d->min_iters_per_unit, d->raster_group, (int)d->fixup,
-                  (int)d->f32_kernel, d->debug_flags & DEBUG_SKIP_PEER_FLAG);
+                  (int)d->f32_kernel, d->debug_flags & DEBUG_SKIP_PEER_FLAG, dev, single ? 1 : 0);
     key = buf;
     for (const Norm &n : work) {
       std::snprintf(buf, sizeof(buf), "%lld,%lld,%lld,%d,%d,%d,%d;", (long long)n.M, (long long)n.N,
@@ -961,6 +1017,11 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
           last_rc = fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
           continue;
         }
+        if (c.fixup == FIXUP_SPLIT_CLUSTER && !xs_runnable(pl, c, work, single, dev, sms)) {
+          last_rc = fail_msg(SK_ERR_UNSUPPORTED,
+                             "cluster split: one BF16 problem, two tile-aligned units per tile, one cluster per tile");
+          continue;
+        }
         double ns = predict_ns(work, pl, c);
         if (ns < best * 0.999) {   // keep the earlier candidate on near-ties
           best = ns;
@@ -999,14 +1060,19 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
               }
             }
             if (d->fixup != SK_FIXUP_OWNER || (d->debug_flags & DEBUG_SKIP_PEER_FLAG) || !split_eligible(pl2)) return;
-            sk_config t3 = t2;
-            t3.fixup = SK_FIXUP_SPLIT;
-            Cfg c3;
-            if (resolve_cfg(fam, &t3, sms, &c3) != SK_OK) return;
-            const double ns3 = predict_ns(work, pl2, c3);
-            if (ns3 < best * 0.999) {
-              best = ns3;
-              best_cfg = t3;
+            // the split reduce through the workspace, and, with two units
+            // per tile, through the clusters' shared memories
+            for (sk_fixup fx : {SK_FIXUP_SPLIT, SK_FIXUP_SPLIT_CLUSTER}) {
+              sk_config t3 = t2;
+              t3.fixup = fx;
+              Cfg c3;
+              if (resolve_cfg(fam, &t3, sms, &c3) != SK_OK) continue;
+              if (fx == SK_FIXUP_SPLIT_CLUSTER && !xs_runnable(pl2, c3, work, single, dev, sms)) continue;
+              const double ns3 = predict_ns(work, pl2, c3);
+              if (ns3 < best * 0.999) {
+                best = ns3;
+                best_cfg = t3;
+              }
             }
           };
           try_units(g_alt, true);
@@ -1049,8 +1115,9 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
 // Normalises the problems, picks the tile (tile_m = 0: auto) and resolves
 // the config.  `work` gets the problems with m, n, k >= 1; `scale_only` the
 // ones with k == 0 (C = beta * C_in).
-sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, int sms, int maxp, Cfg *c,
-                  std::vector<Norm> *work, std::vector<int> *idx, std::vector<Norm> *scale_only) {
+sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, int sms, int maxp, int dev,
+                  bool single, Cfg *c, std::vector<Norm> *work, std::vector<int> *idx,
+                  std::vector<Norm> *scale_only) {
   if (!problems || count < 1 || count > maxp) return SK_ERR_INVALID_ARG;
   for (int i = 0; i < count; ++i) {
     sk_status rc = check_problem(&problems[i]);
@@ -1081,7 +1148,7 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
     for (const Norm &n : *work) tc_ok = tc_ok && check_tc_alignment(n) == SK_OK;
     d.f32_kernel = tc_ok ? SK_F32_TF32X3 : SK_F32_FFMA;
   }
-  sk_status rc = choose_auto(fam, *work, *idx, sms, &d);
+  sk_status rc = choose_auto(fam, *work, *idx, sms, dev, single, &d);
   if (rc != SK_OK) return rc;
   rc = resolve_cfg(fam, &d, sms, c);
   if (rc != SK_OK) return rc;
@@ -1157,7 +1224,7 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   Cfg c;
   std::vector<Norm> work, scale_only;
   std::vector<int> idx;
-  rc = prepare(problems, count, cfg, di.sms, maxp, &c, &work, &idx, &scale_only);
+  rc = prepare(problems, count, cfg, di.sms, maxp, dev, count == 1 && maxp == 1, &c, &work, &idx, &scale_only);
   if (rc != SK_OK) return rc;
   const bool grouped = !(work.size() == 1 && maxp == 1);
   if (c.pair && !work.empty()) {
@@ -1180,6 +1247,9 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   build_plan(work, idx, c, &pl);
   if (c.fixup == FIXUP_SPLIT && !split_eligible(pl))
     return fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
+  if (c.fixup == FIXUP_SPLIT_CLUSTER && !xs_runnable(pl, c, work, !grouped, dev, di.sms))
+    return fail_msg(SK_ERR_UNSUPPORTED,
+                    "cluster split: one BF16 problem, two tile-aligned units per tile, one cluster per tile");
   Workspace w = carve(ws, c);
   void *table = static_cast<uint8_t *>(ws) + ws_base_bytes(c);   // used for groups beyond MAXP_GROUPED
   if (c.fam == FAM_F32 && !c.tc32) {
@@ -1204,7 +1274,7 @@ sk_status plan_for_query(const sk_problem *problems, int count, const sk_config 
   }
   std::vector<Norm> work;
   std::vector<int> idx;
-  sk_status rc = prepare(problems, count, cfg, sms, MAX_PROBLEMS, c, &work, &idx, nullptr);
+  sk_status rc = prepare(problems, count, cfg, sms, MAX_PROBLEMS, dev, count == 1, c, &work, &idx, nullptr);
   if (rc != SK_OK) return rc;
   if (c->pair && dev >= 0 && !work.empty()) {
     const int maxc = pair_clusters(dev, *c, work[0].c_type == SK_F32, count > 1);
@@ -1212,6 +1282,8 @@ sk_status plan_for_query(const sk_problem *problems, int count, const sk_config 
   }
   build_plan(work, idx, *c, pl);
   if (c->fixup == FIXUP_SPLIT && !work.empty() && !split_eligible(*pl)) return SK_ERR_UNSUPPORTED;
+  if (c->fixup == FIXUP_SPLIT_CLUSTER && !work.empty() && !xs_runnable(*pl, *c, work, count == 1, dev, sms))
+    return SK_ERR_UNSUPPORTED;
   pl->predicted_ns = work.empty() ? 0.0 : predict_ns(work, *pl, *c);
   return SK_OK;
 }
@@ -1360,8 +1432,10 @@ sk_status sk_plan_query(const sk_problem *problems, int count, const sk_config *
   out->extra_units = pl.s.r;
   out->workspace_bytes = ws_bytes_for(c, (size_t)pl.s.num_problems);
   out->predicted_us = pl.predicted_ns * 1e-3;
-  out->fixup = c.fixup == FIXUP_SPLIT ? SK_FIXUP_SPLIT : c.fixup == FIXUP_LAST_ARRIVER ? SK_FIXUP_LAST_ARRIVER
-                                                                                         : SK_FIXUP_OWNER;
+  out->fixup = c.fixup == FIXUP_SPLIT_CLUSTER ? SK_FIXUP_SPLIT_CLUSTER
+               : c.fixup == FIXUP_SPLIT       ? SK_FIXUP_SPLIT
+               : c.fixup == FIXUP_LAST_ARRIVER ? SK_FIXUP_LAST_ARRIVER
+                                               : SK_FIXUP_OWNER;
   out->coverage_words = total_iters(pl) + pl.s.total_tiles * (int64_t)(c.BM / 32) * (c.BN / 32);
   return SK_OK;
 }

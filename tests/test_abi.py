@@ -115,8 +115,13 @@ def test_workspace_size(sk):
         c = sk.api._cfg({"num_ctas": 148, "tile_m": tile[0], "tile_n": tile[1], "fixup": "last_arriver"})
         assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
         assert n.value == 256 + 4096 + 2 * 148 * 128 * tile[1] * 4
-    c = sk.api._cfg({"num_ctas": 148, "fixup": 3})
+    c = sk.api._cfg({"num_ctas": 148, "fixup": 4})
     assert B.sk_workspace_size(ctypes.byref(p), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_INVALID_ARG
+    # the cluster split exchanges partials between shared memories: no slots
+    q = sk.shape_problem(1536, 1536, 8192)
+    c = sk.api._cfg({"num_ctas": 144, "tile_m": 256, "mode": "sk", "fixup": "split_cluster"})
+    assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+    assert n.value == 256 + 4096
 
 
 def test_split_reduce_eligibility(sk):
@@ -480,3 +485,34 @@ def test_coverage_words(sk):
         ntiles = sum(tm * tn for tm, tn in tiles)
         assert info.coverage_words == iters + ntiles * (BM // 32) * (BN // 32)
     assert B.sk_config().coverage is None   # NULL by default: the normal kernels run
+
+
+def test_cluster_split_eligibility(sk):
+    """SK_FIXUP_SPLIT_CLUSTER runs only where every tile has exactly two
+    tile-aligned units, on one BF16 problem, with 128-row tiles or 256 x 256
+    pairs; elsewhere the request is SK_ERR_UNSUPPORTED."""
+    B = sk.binding
+
+    def q(shape, cfg, dtype="bf16", count=1):
+        probs = [sk.shape_problem(*shape, dtype=dtype)] * count
+        arr = (B.sk_problem * count)(*probs)
+        info = B.sk_plan_info()
+        c = sk.api._cfg(cfg)
+        return B.sk_plan_query(arr, count, ctypes.byref(c), 152, ctypes.byref(info)), info
+
+    xs = {"mode": "sk", "fixup": "split_cluster"}
+    # 36 tiles of 256 x 256 on 72 pairs, 64 k-blocks each: eligible
+    rc, info = q((1536, 1536, 8192), {**xs, "tile_m": 256, "num_ctas": 144})
+    assert rc == B.SK_OK and info.fixup == B.SK_FIXUP_SPLIT_CLUSTER and info.num_ctas == 2 * info.tiles
+    # 64 tiles of 128 x 128 on 128 CTAs
+    rc, info = q((128, 8192, 16384), {**xs, "tile_m": 128, "tile_n": 128, "num_ctas": 128})
+    assert rc == B.SK_OK and info.fixup == B.SK_FIXUP_SPLIT_CLUSTER
+    # not two units per tile, three units per tile, FP32, E4M3, 256 x 128 pairs, two problems
+    for shape, cfg, dt, cnt in [((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 152}, "bf16", 1),
+                                ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 108}, "bf16", 1),
+                                ((384, 384, 2048), {"tile_m": 128, "num_ctas": 18}, "f32", 1),
+                                ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 144}, "e4m3", 1),
+                                ((1536, 1536, 8192), {"tile_m": 256, "tile_n": 128, "num_ctas": 144}, "bf16", 1),
+                                ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 144}, "bf16", 2)]:
+        rc, _ = q(shape, {**xs, **cfg}, dtype=dt, count=cnt)
+        assert rc == B.SK_ERR_UNSUPPORTED, (shape, cfg, dt, cnt)

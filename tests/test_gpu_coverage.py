@@ -134,6 +134,16 @@ def test_coverage_split_reduce(m, shape, tile, ctas):
     assert info.fixup == m.binding.SK_FIXUP_SPLIT
 
 
+@pytest.mark.parametrize("shape,tile,ctas", [((384, 384, 2048), (128, 128), 18),
+                                             ((700, 900, 1024), (128, 256), 48),
+                                             ((1536, 1536, 8192), (256, 256), 144)])
+def test_coverage_cluster_split(m, shape, tile, ctas):
+    cfg = m.Config(mode="sk", tile_m=tile[0], tile_n=tile[1], num_ctas=ctas, fixup="split_cluster",
+                   min_iters_per_unit=1)
+    info = _check(m, [shape], cfg)
+    assert info.fixup == m.binding.SK_FIXUP_SPLIT_CLUSTER
+
+
 @pytest.mark.parametrize("shape", [(1536, 1536, 2048), (128, 4096, 4096), (1000, 1000, 1000), (384, 384, 2048)])
 def test_coverage_library_default(m, shape):
     """The tile, mode, unit count and fixup the library picks by itself."""
