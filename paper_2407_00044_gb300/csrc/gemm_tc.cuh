@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
   uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage split (one per stage; the leader's in a pair)
   uint64_t *xr_bar = conv_bar + (X3 ? stages : 0);   // XS: the partner's ring is free to write
-  uint64_t *xd_bar = xr_bar + 1;                      // XS: the partner's half has arrived
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + 1);
+  uint64_t *xd_bar = xr_bar + 1;                      // XS: a 64-column group of the partner's half has arrived (2)
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + 2);
   volatile uint32_t *abort_flag = tmem_slot + 1;
   volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
   volatile uint32_t *fix_fail = tmem_slot + 4;   // two words: a staged-sum group failed
@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
     if constexpr (XS) {
       mbar_init(smem_u32(xr_bar), 1);   // the partner's one remote arrival
-      mbar_init(smem_u32(xd_bar), 1);   // this CTA's arrive.expect_tx
+      mbar_init(smem_u32(xd_bar), 1);   // this CTA's arrive.expect_tx, one per group
+      mbar_init(smem_u32(xd_bar + 1), 1);
     }
     if constexpr (X3)   // the 4 epilogue warps of this CTA (of both CTAs in a pair)
       for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), PAIR ? 8 : 4);
@@ -802,20 +803,26 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       if (XS && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
         // Cluster split (the host launches it only when every tile has
         // exactly two contributors, the owner jx = 0 and its peer jx = 1,
-        // and they are the cluster's two units).  Contributor jx sums
-        // columns [jx BN/2, (jx+1) BN/2) of its 128 rows: it writes the
-        // other half of its accumulator into the partner CTA's operand ring
-        // (free once the partner's MMAs are done, which the partner
-        // signals) in TMEM-fragment order, 16 KB per 32-column chunk, and
-        // receives its own half's other partial the same way.  C = alpha
-        // (P0 + P1): one addition, so the result is bit-identical to the
-        // other protocols whichever term comes first.
-        constexpr int HCH = BN / 64;                       // 32-column chunks per half
+        // they are the cluster's two units, and the operand ring holds two
+        // halves).  Contributor jx sums columns [jx BN/2, (jx+1) BN/2) of
+        // its 128 rows.  The other half of its accumulator goes, 64 columns
+        // at a time, TMEM -> registers -> the upper part of its own idle
+        // ring (TMEM-fragment order: each warp's 32 rows of a 32-column
+        // chunk are one contiguous 4 KB block) -> one bulk copy per block
+        // into the bottom of the partner's ring, counted on the partner's
+        // per-group barrier; the partner's ring is free once its MMAs are
+        // done, which it signals.  Then each group of this CTA's own half
+        // is summed as soon as the partner's copy of it has landed.  C =
+        // alpha (P0 + P1): one addition, so the result is bit-identical to
+        // the other protocols whichever term comes first.
+        constexpr int HCH = BN / 64;             // 32-column chunks per half
+        constexpr int NG = HCH / 2;              // 64-column groups per half (one barrier each)
+        constexpr uint32_t CHUNK = 128 * 32 * 4;   // one chunk of 128 rows, FP32
         const int jx = w.role == ROLE_OWNER ? 0 : 1;
         const int own_c0 = jx * HCH, oth_c0 = (1 - jx) * HCH;
         const uint32_t partner = crank ^ (PAIR ? 2u : 1u);
         if (et == 0) {
-          mbar_arrive_expect_tx(smem_u32(xd_bar), (uint32_t)(HCH * 16384));
+          for (int g = 0; g < NG; ++g) mbar_arrive_expect_tx(smem_u32(xd_bar + g), 2 * CHUNK);
           mbar_arrive_cluster(mapa_shared(smem_u32(xr_bar), partner));   // this ring is free
         }
         // (cluster-scope acquires: the arrival and the data come from the partner)
@@ -824,42 +831,51 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           if (et == 0) fail();
         } else {
           const uint32_t rring = mapa_shared(tiles_addr, partner);
-          const uint32_t rbar = mapa_shared(smem_u32(xd_bar), partner);
+          const uint32_t stg_addr = tiles_addr + HCH * CHUNK;
+          float4 *const stg = reinterpret_cast<float4 *>(smem + HCH * CHUNK);
 #pragma unroll 1
-          for (int c = 0; c < HCH; c += 2) {
+          for (int g = 0; g < NG; ++g) {
             float v[64];
-            tmem_ld64(tbase + (oth_c0 + c) * 32, v);
+            tmem_ld64(tbase + (oth_c0 + 2 * g) * 32, v);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
               for (int j = 0; j < 8; ++j)
-                st_async_v4(rring + (uint32_t)(((((c + h) * 4 + q4) * 8 + j) * 32 + lane) * 16),
-                            make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2],
-                                        v[32 * h + 4 * j + 3]),
-                            rbar);
+                stg[(((2 * g + h) * 4 + q4) * 8 + j) * 32 + lane] =
+                    make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2], v[32 * h + 4 * j + 3]);
+            fence_proxy_async_smem_cta();   // the generic writes, to the copy engine
+            __syncwarp();
+            if (lane == 0) {
+              const uint32_t rbar = mapa_shared(smem_u32(xd_bar + g), partner);
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const uint32_t off = (uint32_t)(((2 * g + h) * 4 + q4) * 4096);
+                bulk_copy_s2cluster(rring + off, stg_addr + off, 4096, rbar);
+              }
+            }
           }
           if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // half sent
-          okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar), 0u, tmo));
-          if (!okx && lane == 0) fail();
-          if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           const float alpha = get_alpha();
           const float4 *rx = reinterpret_cast<const float4 *>(smem);
 #pragma unroll 1
-          for (int c = 0; c < HCH; c += 2) {
+          for (int g = 0; g < NG; ++g) {
+            okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar + g), 0u, tmo));
+            if (!okx && lane == 0) fail();
+            if (tr_lead && g == 0 && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
             float v[64];
-            tmem_ld64(tbase + (own_c0 + c) * 32, v);
+            tmem_ld64(tbase + (own_c0 + 2 * g) * 32, v);
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
               for (int j = 0; j < 8; ++j) {
-                const float4 q = rx[(((c + h) * 4 + q4) * 8 + j) * 32 + lane];
+                const float4 q = rx[(((2 * g + h) * 4 + q4) * 8 + j) * 32 + lane];
                 v[32 * h + 4 * j] += q.x;
                 v[32 * h + 4 * j + 1] += q.y;
                 v[32 * h + 4 * j + 2] += q.z;
                 v[32 * h + 4 * j + 3] += q.w;
               }
-            store_chunk(own_c0 + c, *reinterpret_cast<const float(*)[32]>(v), alpha);
-            store_chunk(own_c0 + c + 1, *reinterpret_cast<const float(*)[32]>(v + 32), alpha);
+            store_chunk(own_c0 + 2 * g, *reinterpret_cast<const float(*)[32]>(v), alpha);
+            store_chunk(own_c0 + 2 * g + 1, *reinterpret_cast<const float(*)[32]>(v + 32), alpha);
           }
         }
         release_acc(acc);

@@ -289,6 +289,17 @@ __device__ __forceinline__ void st_async_v4(uint32_t cluster_addr, float4 v, uin
                : "memory");
 }
 
+// Bulk copy from this CTA's shared memory into the shared memory of a CTA
+// of this cluster (shared::cluster destination), counted by complete_tx on
+// that CTA's mbarrier.  Addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_copy_s2cluster(uint32_t dst_cluster, uint32_t src, uint32_t bytes,
+                                                    uint32_t bar_cluster) {
+  asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   dst_cluster),
+               "r"(src), "r"(bytes), "r"(bar_cluster)
+               : "memory");
+}
+
 // All threads of every CTA of the cluster.
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");

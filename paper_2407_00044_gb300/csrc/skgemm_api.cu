@@ -454,8 +454,11 @@ bool split_eligible(const PlanOut &pl) {
 // kernels), every tile split into exactly two ranges (2 units per tile),
 // and a tile shape with a cluster-split kernel.
 bool xs_eligible(const PlanOut &pl, const Cfg &c) {
+  // the operand ring holds the partner's half (incoming) and this CTA's
+  // staged half (outgoing): 128 rows x BN/2 FP32 columns each
+  const int ring = c.stages * (128 * 128 + (c.pair ? c.BN / 2 : c.BN) * 128);
   return pl.s.num_problems == 1 && c.fam == FAM_BF16 && (!c.pair || c.BN == 256) && split_eligible(pl) &&
-         (int64_t)pl.s.g == 2 * pl.s.total_tiles;
+         (int64_t)pl.s.g == 2 * pl.s.total_tiles && ring >= 2 * 128 * (c.BN / 2) * 4;
 }
 
 double algorithmic_dram_bytes(const std::vector<Norm> &work) {
