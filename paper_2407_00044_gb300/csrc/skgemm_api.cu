@@ -412,11 +412,14 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // BF16 rate per k-block plus the in-kernel split of the stage; the
 // epilogue warps also do the split, so an epilogue does not overlap the
 // next item's MMAs).
-#define TF32X3_COEFFS 430.0, 900.0, 5160.0, 4500.0, 3020.0, 0.0, 3210.0, 790.0
+#define TF32X3_COEFFS 700.0, 900.0, 5160.0, 4500.0, 3020.0, 0.0, 3210.0, 790.0
 // 3xTF32 on CTA pairs (256 x 256 tiles): twelve M = 256 TF32 MMAs per
 // 32-deep k-block (1536 cycles), the split spread over both CTAs' epilogue
-// warps.
-#define TF32X3_PAIR_COEFFS 900.0, 1190.0, 8500.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0
+// warps.  The per-k-block costs of both 3xTF32 families are refitted to
+// seven FP32 shapes timed on GB300 (384x384x2048 to 8192x4096x4096): the
+// model then ranks the two tiles as measured on all seven (pairs win from
+// 1024x1024x4096 up, e.g. 4096^3 505 against 643 us).
+#define TF32X3_PAIR_COEFFS 1100.0, 1190.0, 8500.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0
 
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
