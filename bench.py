@@ -232,7 +232,10 @@ def run_ours(args, world, rank, local):
         per_shape = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(steps)] for i in range(len(shapes))]
         return per_shape
 
-    auto = sk.Config(mode=args.mode)
+    # (--fixup / --num-ctas / --tile pin the Stream-K arm's protocol and plan,
+    # e.g. to profile one fixup; by default the library chooses)
+    tm, tn = (int(x) for x in args.tile.split("x")) if args.tile else (0, 0)
+    auto = sk.Config(mode=args.mode, fixup=args.fixup, num_ctas=args.num_ctas, tile_m=tm, tile_n=tn)
     dp = sk.Config(mode="dp")
     for _ in range(args.warmup):
         one_pass(auto)
@@ -755,6 +758,10 @@ def main(argv=None):
     ap.add_argument("--only", default="", help="M,N,K: time this one problem instead of the sweep "
                     "(with --workload f32: instead of 384,384,2048)")
     ap.add_argument("--mode", default="auto", choices=["auto", "dp", "sk", "hybrid1", "hybrid2"])
+    ap.add_argument("--fixup", default="owner", choices=["owner", "last_arriver", "split", "split_cluster"],
+                    help="fixup of the Stream-K arm ('owner' lets the library choose among all)")
+    ap.add_argument("--num-ctas", type=int, default=0, help="CTAs of the Stream-K arm (0 = library)")
+    ap.add_argument("--tile", default="", help="tile of the Stream-K arm as MxN, e.g. 256x256 (default: library)")
     ap.add_argument("--no-dp", dest="dp", action="store_false", help="skip the data-parallel baseline")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false", help="skip the host-buffer run")
     ap.add_argument("--no-configs", dest="configs", action="store_false",
