@@ -82,9 +82,11 @@ def _signature(info):
 
 def candidates(problem: B.sk_problem, num_sms: int = 0):
     """All valid configs with their predicted time, fastest first.  FP32
-    problems try both FP32 kernels; where every tile is split and there
-    are fewer tiles than units, the largest multiple of the tile count is
-    tried as well, with the owner fixup and with the split reduce."""
+    problems try both FP32 kernels (3xTF32 on 128 x 128 tiles and on CTA
+    pairs); where every tile is split and there are fewer tiles than units,
+    the largest multiple of the tile count is tried as well, with the owner
+    fixup and with the split reduce, and twice the tile count with the
+    cluster split."""
     out = []
     seen = set()
 
@@ -101,9 +103,10 @@ def candidates(problem: B.sk_problem, num_sms: int = 0):
                 for fk in f32_kernels:
                     cfg = api.Config(tile_m=tm, tile_n=tn, stages=st, mode=mode, f32_kernel=fk)
                     if problem.a_type == B.SK_F32:
-                        if (tm, tn) != (128, 128) or st != 6:
+                        if st != _STAGES[(tm, tn)][0] or (tm, tn) not in ((128, 128), (256, 256)) or (
+                                fk == "ffma" and tm != 128):
                             continue
-                        cfg = api.Config(tile_m=128, tile_n=128, mode=mode, f32_kernel=fk)
+                        cfg = api.Config(tile_m=tm, tile_n=tn, mode=mode, f32_kernel=fk)
                     info = _try(problem, cfg, num_sms)
                     if info is None:
                         continue
@@ -114,11 +117,12 @@ def candidates(problem: B.sk_problem, num_sms: int = 0):
                     T, g = info.tiles, info.num_ctas
                     if info.sk_tiles == T and 0 < T and 2 * T <= g:
                         per = 2 if cfg.tile_m == 256 else 1
-                        for fx in ("owner", "split"):
-                            if fx == "owner" and g // T * T == g:
+                        for fx in ("owner", "split", "split_cluster"):
+                            units = 2 * T if fx == "split_cluster" else g // T * T
+                            if fx == "owner" and units == g:
                                 continue   # the plan above
                             cfg2 = api.Config(tile_m=cfg.tile_m, tile_n=cfg.tile_n, stages=cfg.stages,
-                                              mode=cfg.mode, num_ctas=per * (g // T * T), fixup=fx,
+                                              mode=cfg.mode, num_ctas=per * units, fixup=fx,
                                               f32_kernel=fk)
                             info2 = _try(problem, cfg2, num_sms)
                             if info2 is not None:

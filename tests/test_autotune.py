@@ -30,9 +30,14 @@ def test_candidates_ranked_and_valid(sk):
     # transposed E4M3 operands are refused by both kernels: no candidates
     p = sk.shape_problem(4096, 4096, 4096, dtype="e4m3", a_layout="col")
     assert sk.autotune.candidates(p, num_sms=152) == []
-    # FP32: one tile
+    # FP32: 128 x 128 tiles (3xTF32 and FFMA) and 256 x 256 pairs (3xTF32 only)
     p = sk.shape_problem(384, 384, 2048, dtype="f32")
-    assert {(cfg.tile_m, cfg.tile_n) for cfg, _ in sk.autotune.candidates(p, num_sms=152)} == {(128, 128)}
+    c = sk.autotune.candidates(p, num_sms=152)
+    assert {(cfg.tile_m, cfg.tile_n) for cfg, _ in c} == {(128, 128), (256, 256)}
+    assert all(cfg.f32_kernel == "tf32x3" for cfg, _ in c if cfg.tile_m == 256)
+    # tiles split in two: the cluster split is among the candidates
+    c = sk.autotune.candidates(sk.shape_problem(1536, 1536, 8192), num_sms=152)
+    assert any(cfg.fixup == "split_cluster" for cfg, _ in c)
 
 
 def test_cache_round_trip(sk, tmp_path):
