@@ -132,16 +132,17 @@ typedef enum {
                                   where its runtime model predicts a gain (no
                                   counterpart in the paper) */
     SK_FIXUP_SPLIT_CLUSTER = 3 /* the split reduce for plans that cut every tile
-                                  into exactly two ranges (2 units per tile):
-                                  the tile's two units run as one thread-block
-                                  cluster (2 CTAs, or 2 CTA pairs) and each writes
-                                  the half of its partial that the other sums
-                                  straight into the other's shared memory -- no
+                                  into k = 2, 4 or 8 equal tile-aligned ranges (k
+                                  units per tile, at most 8 CTAs): the tile's k
+                                  units run as one thread-block cluster and each
+                                  writes the parts of its partial that the others
+                                  sum straight into their shared memories -- no
                                   workspace slots or flags.  Single-problem BF16
-                                  calls on 128-row tiles or 256 x 256 pairs, with
-                                  one co-resident cluster per tile; otherwise
-                                  SK_ERR_UNSUPPORTED.  Chosen by the library like
-                                  SK_FIXUP_SPLIT (no counterpart in the paper) */
+                                  or 3xTF32 calls on 128-row tiles or 256 x 256
+                                  pairs; otherwise SK_ERR_UNSUPPORTED.  The
+                                  library picks it by itself (like SK_FIXUP_SPLIT)
+                                  with k = 2 and one co-resident cluster per tile
+                                  (no counterpart in the paper) */
 } sk_fixup;
 
 /* Kernel for FP32 problems. */

@@ -115,7 +115,7 @@ struct TcParams {
   uint32_t *cover;      // optional coverage counts (SK_COVERAGE in skgemm.h)
   int64_t cover_iters;  // MAC-loop iterations of all problems: the first block-store word
   int32_t fixup;
-  int32_t pad_;
+  int32_t xs_k;         // FIXUP_SPLIT_CLUSTER: units per tile (= per cluster), 2, 4 or 8
 };
 
 // Coverage word increment of one visit by unit u (SK_COVERAGE_VISIT).
@@ -163,9 +163,9 @@ template <int IN, typename OutT, int BN, int MAXP>
 int pair_max_clusters(int stages);
 
 // Co-resident clusters of the cluster-split kernel (FIXUP_SPLIT_CLUSTER,
-// single-problem BF16): two units per cluster.
-template <typename OutT, int BN, bool PAIR>
-int xs_max_clusters(int stages);
+// single problem): xs_k units (CTAs or CTA pairs) per cluster.
+template <int IN, typename OutT, int BN, bool PAIR>
+int xs_max_clusters(int stages, int xs_k);
 
 cudaError_t launch_scale(void *C, const void *C_in, int64_t ldc, int64_t M, int64_t N,
                          float beta, int c_is_f32, cudaStream_t st);

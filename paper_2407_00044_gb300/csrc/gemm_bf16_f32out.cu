@@ -5,6 +5,6 @@
 namespace sk {
 template cudaError_t launch_tc<IN_BF16, float, 256, 1, false>(const TcParams<1> &, int, cudaStream_t);
 template cudaError_t launch_tc<IN_BF16, float, 128, 1, false>(const TcParams<1> &, int, cudaStream_t);
-template int xs_max_clusters<float, 256, false>(int);
-template int xs_max_clusters<float, 128, false>(int);
+template int xs_max_clusters<IN_BF16, float, 256, false>(int, int);
+template int xs_max_clusters<IN_BF16, float, 128, false>(int, int);
 }  // namespace sk

@@ -8,6 +8,6 @@ template cudaError_t launch_tc<IN_BF16, __nv_bfloat16, 256, 1, true>(const TcPar
 template cudaError_t launch_tc<IN_BF16, float, 256, 1, true>(const TcParams<1> &, int, cudaStream_t);
 template int pair_max_clusters<IN_BF16, __nv_bfloat16, 256, 1>(int);
 template int pair_max_clusters<IN_BF16, float, 256, 1>(int);
-template int xs_max_clusters<__nv_bfloat16, 256, true>(int);
-template int xs_max_clusters<float, 256, true>(int);
+template int xs_max_clusters<IN_BF16, __nv_bfloat16, 256, true>(int, int);
+template int xs_max_clusters<IN_BF16, float, 256, true>(int, int);
 }  // namespace sk

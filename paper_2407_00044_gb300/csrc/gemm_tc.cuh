@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
   uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage split (one per stage; the leader's in a pair)
   uint64_t *xr_bar = conv_bar + (X3 ? stages : 0);   // XS: the partner's ring is free to write
-  uint64_t *xd_bar = xr_bar + 1;                      // XS: a 64-column group of the partner's half has arrived (2)
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + 2);
+  uint64_t *xd_bar = xr_bar + 1;                      // XS: every partner's blocks have arrived
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + 1);
   volatile uint32_t *abort_flag = tmem_slot + 1;
   volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
   volatile uint32_t *fix_fail = tmem_slot + 4;   // two words: a staged-sum group failed
@@ -193,9 +193,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  // CTAs per cluster: a pair (2), or, XS, two units (4 CTAs or 2)
-  constexpr int CL = XS ? (PAIR ? 4 : 2) : (PAIR ? 2 : 1);
-  const uint32_t crank = CL > 1 ? cluster_ctarank() : 0u;
+  // clusters: a CTA pair, or, XS, the P.xs_k units of a tile (CTAs or pairs)
+  constexpr bool CLUSTER = XS || PAIR;
+  const uint32_t crank = CLUSTER ? cluster_ctarank() : 0u;
   const uint32_t rank = PAIR ? (XS ? (crank & 1u) : crank) : 0u;   // this CTA within its pair
   const uint32_t pbase = (PAIR && XS) ? (crank & ~1u) : 0u;        // cluster rank of its pair's leader
   const bool leader = rank == 0;
@@ -223,9 +223,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     mbar_init(smem_u32(done_bar), 1);
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
     if constexpr (XS) {
-      mbar_init(smem_u32(xr_bar), 1);   // the partner's one remote arrival
-      mbar_init(smem_u32(xd_bar), 1);   // this CTA's arrive.expect_tx, one per group
-      mbar_init(smem_u32(xd_bar + 1), 1);
+      mbar_init(smem_u32(xr_bar), (uint32_t)(P.xs_k - 1));   // one remote arrival per partner
+      mbar_init(smem_u32(xd_bar), 1);                        // this CTA's arrive.expect_tx
     }
     if constexpr (X3)   // the 4 epilogue warps of this CTA (of both CTAs in a pair)
       for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), PAIR ? 8 : 4);
@@ -245,7 +244,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   }
   tc_fence_before();
   cta_sync();
-  if constexpr (CL > 1) cluster_sync();   // the other CTAs' barriers exist before anyone signals them
+  if constexpr (CLUSTER) cluster_sync();   // the other CTAs' barriers exist before anyone signals them
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   // Timeline tracing and coverage counting are compiled only into the DBG
@@ -802,80 +801,106 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
       int o = u, pl = w.peer_last;
       if (XS && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
         // Cluster split (the host launches it only when every tile has
-        // exactly two contributors, the owner jx = 0 and its peer jx = 1,
-        // they are the cluster's two units, and the operand ring holds two
-        // halves).  Contributor jx sums columns [jx BN/2, (jx+1) BN/2) of
-        // its 128 rows.  The other half of its accumulator goes, 64 columns
-        // at a time, TMEM -> registers -> the upper part of its own idle
-        // ring (TMEM-fragment order: each warp's 32 rows of a 32-column
-        // chunk are one contiguous 4 KB block) -> one bulk copy per block
-        // into the bottom of the partner's ring, counted on the partner's
-        // per-group barrier; the partner's ring is free once its MMAs are
-        // done, which it signals.  Then each group of this CTA's own half
-        // is summed as soon as the partner's copy of it has landed.  C =
-        // alpha (P0 + P1): one addition, so the result is bit-identical to
-        // the other protocols whichever term comes first.
-        constexpr int HCH = BN / 64;             // 32-column chunks per half
-        constexpr int NG = HCH / 2;              // 64-column groups per half (one barrier each)
-        constexpr uint32_t CHUNK = 128 * 32 * 4;   // one chunk of 128 rows, FP32
-        const int jx = w.role == ROLE_OWNER ? 0 : 1;
-        const int own_c0 = jx * HCH, oth_c0 = (1 - jx) * HCH;
-        const uint32_t partner = crank ^ (PAIR ? 2u : 1u);
+        // exactly kc = P.xs_k contributors (2, 4 or 8), they are the
+        // cluster's kc units in unit order (contributor jx = u - o holds
+        // k-range jx; jx = 0 is the owner), and the operand ring holds the
+        // exchanged blocks).  The tile's (column group x warp) units are
+        // dealt out as in the split reduce: unit s is 32-column chunk group
+        // s / 4 (UW chunks) of warp s % 4, contributor j sums units
+        // [j NS / kc, (j+1) NS / kc).  Each warp sends the blocks of its
+        // units that other contributors sum -- TMEM -> registers -> a
+        // staging block in its own idle ring (TMEM-fragment order, 4 KB per
+        // chunk) -> one bulk copy into the receiver's ring, counted on the
+        // receiver's data barrier -- once every partner has signalled that
+        // its MMAs are done (its ring is free).  Then each warp sums its own
+        // units from the kc partials in ascending contributor order (its
+        // own from TMEM at its place), the order every other protocol uses,
+        // so C is bit-identical to them.
+        constexpr int UW = sizeof(OutT) == 4 ? 1 : 2;   // 32-column chunks per unit
+        constexpr int NS = 4 * (BN / 32) / UW;          // units of the tile
+        constexpr uint32_t BLK = UW * 4096;             // one unit of one partial
+        const int kc = P.xs_k;
+        const int jx = (int)(PAIR ? (crank >> 1) : crank);
+        auto s_lo = [&](int j) { return j * NS / kc; };
+        auto cta_of = [&](int j) { return (uint32_t)(PAIR ? 2 * j + (int)rank : j); };
+        const int s0 = s_lo(jx), s1 = s_lo(jx + 1), own_n = s1 - s0;
+        // ring: [incoming: (kc - 1) sources x own_n units][outgoing staging:
+        // the other contributors' units in unit order]
+        const uint32_t out_base = (uint32_t)((kc - 1) * own_n) * BLK;
         if (et == 0) {
-          for (int g = 0; g < NG; ++g) mbar_arrive_expect_tx(smem_u32(xd_bar + g), 2 * CHUNK);
-          mbar_arrive_cluster(mapa_shared(smem_u32(xr_bar), partner));   // this ring is free
+          mbar_arrive_expect_tx(smem_u32(xd_bar), out_base);   // incoming bytes
+          for (int i = 0; i < kc; ++i)
+            if (i != jx) mbar_arrive_cluster(mapa_shared(smem_u32(xr_bar), cta_of(i)));   // this ring is free
         }
-        // (cluster-scope acquires: the arrival and the data come from the partner)
+        // (cluster-scope acquires: the arrivals and the data come from the partners)
         bool okx = mbar_wait_cluster(smem_u32(xr_bar), 0u, tmo);
         if (named_bar_or(1, 128, !okx)) {
           if (et == 0) fail();
         } else {
-          const uint32_t rring = mapa_shared(tiles_addr, partner);
-          const uint32_t stg_addr = tiles_addr + HCH * CHUNK;
-          float4 *const stg = reinterpret_cast<float4 *>(smem + HCH * CHUNK);
 #pragma unroll 1
-          for (int g = 0; g < NG; ++g) {
-            float v[64];
-            tmem_ld64(tbase + (oth_c0 + 2 * g) * 32, v);
+          for (int s = q4; s < NS; s += 4) {
+            if (s >= s0 && s < s1) continue;
+            int i = s * kc / NS;   // the contributor that sums unit s
+            while (s_lo(i + 1) <= s) ++i;
+            while (s_lo(i) > s) --i;
+            const int own_i = s_lo(i + 1) - s_lo(i);
+            const uint32_t src_slot = (uint32_t)(jx < i ? jx : jx - 1);   // this CTA among i's sources
+            const uint32_t dst_off = (src_slot * (uint32_t)own_i + (uint32_t)(s - s_lo(i))) * BLK;
+            const uint32_t stg_off = out_base + (uint32_t)(s - (s >= s1 ? own_n : 0)) * BLK;
+            float4 *const stg = reinterpret_cast<float4 *>(smem + stg_off);
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < UW; ++h) {
+              float v[32];
+              tmem_ld32(tbase + ((s / 4) * UW + h) * 32, v);
 #pragma unroll
               for (int j = 0; j < 8; ++j)
-                stg[(((2 * g + h) * 4 + q4) * 8 + j) * 32 + lane] =
-                    make_float4(v[32 * h + 4 * j], v[32 * h + 4 * j + 1], v[32 * h + 4 * j + 2], v[32 * h + 4 * j + 3]);
+                stg[(h * 8 + j) * 32 + lane] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
             fence_proxy_async_smem_cta();   // the generic writes, to the copy engine
             __syncwarp();
-            if (lane == 0) {
-              const uint32_t rbar = mapa_shared(smem_u32(xd_bar + g), partner);
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const uint32_t off = (uint32_t)(((2 * g + h) * 4 + q4) * 4096);
-                bulk_copy_s2cluster(rring + off, stg_addr + off, 4096, rbar);
-              }
-            }
+            if (lane == 0)
+              bulk_copy_s2cluster(mapa_shared(tiles_addr + dst_off, cta_of(i)), tiles_addr + stg_off, BLK,
+                                  mapa_shared(smem_u32(xd_bar), cta_of(i)));
           }
-          if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // half sent
+          if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // blocks sent
+          okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar), 0u, tmo));
+          if (!okx && lane == 0) fail();
+          if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           const float alpha = get_alpha();
-          const float4 *rx = reinterpret_cast<const float4 *>(smem);
 #pragma unroll 1
-          for (int g = 0; g < NG; ++g) {
-            okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar + g), 0u, tmo));
-            if (!okx && lane == 0) fail();
-            if (tr_lead && g == 0 && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
-            float v[64];
-            tmem_ld64(tbase + (own_c0 + 2 * g) * 32, v);
+          for (int s = s0 + ((q4 - s0 % 4) + 4) % 4; s < s1; s += 4) {   // this warp's own units
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < UW; ++h) {
+              float v[32];
+              for (int i = 0; i < kc; ++i) {
+                if (i == jx) {
+                  float t[32];
+                  tmem_ld32(tbase + ((s / 4) * UW + h) * 32, t);
 #pragma unroll
-              for (int j = 0; j < 8; ++j) {
-                const float4 q = rx[(((2 * g + h) * 4 + q4) * 8 + j) * 32 + lane];
-                v[32 * h + 4 * j] += q.x;
-                v[32 * h + 4 * j + 1] += q.y;
-                v[32 * h + 4 * j + 2] += q.z;
-                v[32 * h + 4 * j + 3] += q.w;
+                  for (int e = 0; e < 32; ++e) v[e] = i == 0 ? t[e] : v[e] + t[e];
+                } else {
+                  const uint32_t src_slot = (uint32_t)(i < jx ? i : i - 1);
+                  const float4 *blk = reinterpret_cast<const float4 *>(
+                      smem + (src_slot * (uint32_t)own_n + (uint32_t)(s - s0)) * BLK);
+#pragma unroll
+                  for (int j = 0; j < 8; ++j) {
+                    const float4 q = blk[(h * 8 + j) * 32 + lane];
+                    if (i == 0) {
+                      v[4 * j] = q.x;
+                      v[4 * j + 1] = q.y;
+                      v[4 * j + 2] = q.z;
+                      v[4 * j + 3] = q.w;
+                    } else {
+                      v[4 * j] += q.x;
+                      v[4 * j + 1] += q.y;
+                      v[4 * j + 2] += q.z;
+                      v[4 * j + 3] += q.w;
+                    }
+                  }
+                }
               }
-            store_chunk(own_c0 + 2 * g, *reinterpret_cast<const float(*)[32]>(v), alpha);
-            store_chunk(own_c0 + 2 * g + 1, *reinterpret_cast<const float(*)[32]>(v + 32), alpha);
+              store_chunk((s / 4) * UW + h, v, alpha);
+            }
           }
         }
         release_acc(acc);
@@ -1179,7 +1204,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   // A pair's leader MMAs read the peer's shared memory and write its TMEM,
   // and XS partners write each other's shared memory: no CTA of a cluster
   // frees TMEM or exits before all are done.
-  if constexpr (CL > 1) cluster_sync();
+  if constexpr (CLUSTER) cluster_sync();
   if (warp == 1) {
     tc_fence_after();
     if constexpr (PAIR)
@@ -1192,12 +1217,13 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR, bool DBG, bool XS>
 cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
   auto kern = sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, DBG, XS>;
-  constexpr int CL = XS ? (PAIR ? 4 : 2) : (PAIR ? 2 : 1);
+  // CTAs per cluster: a pair, or, XS, the xs_k units of a tile
+  const int cl = XS ? (PAIR ? 2 : 1) * p.xs_k : (PAIR ? 2 : 1);
   const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, p.stages, IN == IN_TF32X3);
   (void)cudaGetLastError();   // drop a stale error left by an earlier call on this thread
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  if constexpr (CL == 1) {
+  if (cl == 1) {
     kern<<<grid, 192, smem, st>>>(p);
     return cudaGetLastError();
   } else {
@@ -1210,7 +1236,7 @@ cudaError_t launch_tc_variant(const TcParams<MAXP> &p, int grid, cudaStream_t st
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.x = (unsigned)cl;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
@@ -1229,10 +1255,11 @@ constexpr bool has_debug_variant() {
 }
 
 // Cluster-split variants (FIXUP_SPLIT_CLUSTER) exist for single-problem
-// BF16 launches on 128 x 128 / 128 x 256 tiles and 256 x 256 pairs.
+// BF16 launches on 128 x 128 / 128 x 256 tiles and 256 x 256 pairs, and
+// for single-problem 3xTF32 launches (128 x 128 tiles, 256 x 256 pairs).
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
 constexpr bool has_xs_variant() {
-  return IN == IN_BF16 && MAXP == 1 && (!PAIR || BN == 256);
+  return (IN == IN_BF16 || IN == IN_TF32X3) && MAXP == 1 && (!PAIR || BN == 256);
 }
 
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
@@ -1253,13 +1280,13 @@ cudaError_t launch_tc(const TcParams<MAXP> &p, int grid, cudaStream_t st) {
 // (xs = false), or, for the cluster split (xs = true), clusters of two
 // units -- four CTAs for pairs, two single CTAs otherwise.
 template <int IN, typename OutT, int BN, int MAXP, bool PAIR>
-int tc_max_clusters(int stages, bool xs) {
+int tc_max_clusters(int stages, bool xs, int xs_k = 2) {
   constexpr bool XS_OK = has_xs_variant<IN, OutT, BN, MAXP, PAIR>();
   if (xs && !XS_OK) return 0;
   if (!xs && !PAIR) return 0;
   auto kern = xs ? sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, false, XS_OK>
                  : sk_tc_kernel<IN, OutT, BN, MAXP, PAIR, false, false>;
-  const int cl = xs ? (PAIR ? 4 : 2) : 2;
+  const int cl = xs ? (PAIR ? 2 : 1) * xs_k : 2;
   const int smem = tc_smem_bytes(PAIR ? BN / 2 : BN, stages, IN == IN_TF32X3);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
@@ -1286,9 +1313,9 @@ int pair_max_clusters(int stages) {
   return tc_max_clusters<IN, OutT, BN, MAXP, true>(stages, false);
 }
 
-template <typename OutT, int BN, bool PAIR>
-int xs_max_clusters(int stages) {
-  return tc_max_clusters<IN_BF16, OutT, BN, 1, PAIR>(stages, true);
+template <int IN, typename OutT, int BN, bool PAIR>
+int xs_max_clusters(int stages, int xs_k) {
+  return tc_max_clusters<IN, OutT, BN, 1, PAIR>(stages, true, xs_k);
 }
 
 }  // namespace sk

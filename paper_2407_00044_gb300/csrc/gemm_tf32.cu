@@ -10,5 +10,7 @@ template cudaError_t launch_tc<IN_TF32X3, float, 256, 1, true>(const TcParams<1>
 template cudaError_t launch_tc<IN_TF32X3, float, 256, MAXP_GROUPED, true>(const TcParams<MAXP_GROUPED> &, int,
                                                                           cudaStream_t);
 template int pair_max_clusters<IN_TF32X3, float, 256, 1>(int);
+template int xs_max_clusters<IN_TF32X3, float, 256, true>(int, int);
+template int xs_max_clusters<IN_TF32X3, float, 128, false>(int, int);
 template int pair_max_clusters<IN_TF32X3, float, 256, MAXP_GROUPED>(int);
 }  // namespace sk

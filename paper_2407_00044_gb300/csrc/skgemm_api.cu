@@ -256,8 +256,10 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
   if (d.fixup != SK_FIXUP_OWNER && d.fixup != SK_FIXUP_LAST_ARRIVER && d.fixup != SK_FIXUP_SPLIT &&
       d.fixup != SK_FIXUP_SPLIT_CLUSTER)
     return SK_ERR_INVALID_ARG;
-  // the cluster split: single-problem BF16 on 128-row tiles or 256 x 256 pairs
-  if (d.fixup == SK_FIXUP_SPLIT_CLUSTER && (fam != FAM_BF16 || (r.pair && r.BN != 256))) return SK_ERR_UNSUPPORTED;
+  // the cluster split: BF16 or 3xTF32 on 128-row tiles or 256 x 256 pairs
+  if (d.fixup == SK_FIXUP_SPLIT_CLUSTER &&
+      (!(fam == FAM_BF16 || (fam == FAM_F32 && r.tc32)) || (r.pair && r.BN != 256)))
+    return SK_ERR_UNSUPPORTED;
   r.fixup = d.fixup == SK_FIXUP_LAST_ARRIVER ? FIXUP_LAST_ARRIVER
             : d.fixup == SK_FIXUP_SPLIT      ? FIXUP_SPLIT
             : d.fixup == SK_FIXUP_SPLIT_CLUSTER ? FIXUP_SPLIT_CLUSTER
@@ -456,12 +458,25 @@ bool split_eligible(const PlanOut &pl) {
 // The cluster split additionally needs one problem (the single-problem
 // kernels), every tile split into exactly two ranges (2 units per tile),
 // and a tile shape with a cluster-split kernel.
-bool xs_eligible(const PlanOut &pl, const Cfg &c) {
-  // the operand ring holds the partner's half (incoming) and this CTA's
-  // staged half (outgoing): 128 rows x BN/2 FP32 columns each
-  const int ring = c.stages * (128 * 128 + (c.pair ? c.BN / 2 : c.BN) * 128);
-  return pl.s.num_problems == 1 && c.fam == FAM_BF16 && (!c.pair || c.BN == 256) && split_eligible(pl) &&
-         (int64_t)pl.s.g == 2 * pl.s.total_tiles && ring >= 2 * 128 * (c.BN / 2) * 4;
+// Units per tile of a cluster-split plan (2, 4 or 8; a cluster holds at
+// most 8 CTAs), or 0 if the plan cannot run as one: one problem, every
+// tile split into equal tile-aligned ranges (split_eligible), a tile shape
+// with a cluster-split kernel, and an operand ring that holds this CTA's
+// incoming blocks ((k - 1) partials of its units) and its outgoing ones.
+int xs_units_per_tile(const PlanOut &pl, const Cfg &c, const std::vector<Norm> &work) {
+  if (pl.s.num_problems != 1 || pl.s.total_tiles <= 0 || !split_eligible(pl)) return 0;
+  if (!(c.fam == FAM_BF16 || (c.fam == FAM_F32 && c.tc32)) || (c.pair && c.BN != 256)) return 0;
+  if (pl.s.g % pl.s.total_tiles != 0) return 0;
+  const int k = (int)(pl.s.g / pl.s.total_tiles);
+  if (k != 2 && k != 4 && k != 8) return 0;
+  if ((c.pair ? 2 : 1) * k > 8) return 0;
+  const int uw = work[0].c_type == SK_F32 ? 1 : 2;   // 32-column chunks per unit
+  const int ns = 4 * (c.BN / 32) / uw;
+  const int blk = uw * 4096;
+  const int own_max = (ns + k - 1) / k, own_min = ns / k;
+  const int stage = (128 * 128 + (c.pair ? c.BN / 2 : c.BN) * 128) * (c.tc32 ? 2 : 1);
+  if ((int64_t)c.stages * stage < (int64_t)((k - 1) * own_max + (ns - own_min)) * blk) return 0;
+  return k;
 }
 
 double algorithmic_dram_bytes(const std::vector<Norm> &work) {
@@ -592,13 +607,17 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
         double start = std::max(mac_end, epi_prev);
         double e;
         if (c.fixup == FIXUP_SPLIT_CLUSTER && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
-          // the two contributors (units o, o + 1) each signal a free ring
-          // when their accumulator is complete, write the other's half
-          // into its shared memory and sum / store their own half
-          const int o = w.role == ROLE_OWNER ? u : u - 1;
+          // the kc contributors (units o .. o + kc - 1, one cluster) each
+          // signal a free ring when their accumulator is complete, write
+          // the (kc - 1) / kc of it the others sum into their shared
+          // memories, then sum and store their 1 / kc of the tile
+          const int kc = (int)(s.g / s.total_tiles);
+          const int o = u - u % kc;
           spill_done[u] = start;
-          if (pass > 0) start = std::max(spill_done[o], spill_done[o + 1]);
-          e = kXsExchangeFrac * k.spill_ns + 0.5 * k.store_ns;
+          if (pass > 0)
+            for (int p = o; p < o + kc; ++p) start = std::max(start, spill_done[p]);
+          e = kXsExchangeFrac * k.spill_ns * 2.0 * (kc - 1) / kc + k.store_ns / kc +
+              (kc > 2 ? k.fix_peer_last_ns * (kc - 2) / kc : 0.0);
         } else if (c.fixup == FIXUP_SPLIT && (w.role == ROLE_PEER || w.role == ROLE_OWNER)) {
           // all contributors spill, wait for each other, then each reads
           // about one partial's bytes and stores its share of the tile
@@ -796,6 +815,7 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   P->cover = c.cover;
   P->cover_iters = total_iters(pl);
   P->fixup = c.fixup;
+  P->xs_k = c.fixup == FIXUP_SPLIT_CLUSTER ? (int32_t)(pl.s.g / std::max<int64_t>(1, pl.s.total_tiles)) : 0;
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
   if (c.fam == FAM_BF16) {
@@ -906,34 +926,46 @@ sk_status launch_f32_family(const std::vector<Norm> &probs, const PlanOut &pl, c
 // mode = AUTO) with the candidate the runtime model predicts fastest.
 // Decisions are cached per problem set and config.
 //
-// Co-resident clusters of the cluster-split kernel (two units each) for
-// config c on device `dev`, cached; with no device (dev < 0: plan queries
-// given an SM count) every SM is assumed usable.
-int xs_capacity(int dev, const Cfg &c, bool f32out, int sms) {
-  const int per = c.pair ? 4 : 2;
+// Co-resident clusters of the cluster-split kernel with k units per
+// cluster for config c on device `dev`, cached; with no device (dev < 0:
+// plan queries given an SM count) every SM is assumed usable.
+int xs_capacity(int dev, const Cfg &c, bool f32out, int sms, int k) {
+  const int per = (c.pair ? 2 : 1) * k;
   if (dev < 0 || dev >= 64) return sms / per;
   static std::mutex mu;
-  static int cache[64][2][2][2][16] = {};
+  static int cache[64][2][2][2][2][4][16] = {};
   std::lock_guard<std::mutex> lk(mu);
-  int &slot = cache[dev][c.pair ? 1 : 0][c.BN == 256 ? 1 : 0][f32out ? 1 : 0][c.stages & 15];
+  const int ki = k == 2 ? 0 : k == 4 ? 1 : k == 8 ? 2 : 3;
+  int &slot = cache[dev][c.tc32 ? 1 : 0][c.pair ? 1 : 0][c.BN == 256 ? 1 : 0][f32out ? 1 : 0][ki][c.stages & 15];
   if (slot == 0) {
     int n;
-    if (c.pair)
-      n = f32out ? xs_max_clusters<float, 256, true>(c.stages) : xs_max_clusters<__nv_bfloat16, 256, true>(c.stages);
+    if (c.tc32)
+      n = c.pair ? xs_max_clusters<IN_TF32X3, float, 256, true>(c.stages, k)
+                 : xs_max_clusters<IN_TF32X3, float, 128, false>(c.stages, k);
+    else if (c.pair)
+      n = f32out ? xs_max_clusters<IN_BF16, float, 256, true>(c.stages, k)
+                 : xs_max_clusters<IN_BF16, __nv_bfloat16, 256, true>(c.stages, k);
     else if (c.BN == 256)
-      n = f32out ? xs_max_clusters<float, 256, false>(c.stages) : xs_max_clusters<__nv_bfloat16, 256, false>(c.stages);
+      n = f32out ? xs_max_clusters<IN_BF16, float, 256, false>(c.stages, k)
+                 : xs_max_clusters<IN_BF16, __nv_bfloat16, 256, false>(c.stages, k);
     else
-      n = f32out ? xs_max_clusters<float, 128, false>(c.stages) : xs_max_clusters<__nv_bfloat16, 128, false>(c.stages);
+      n = f32out ? xs_max_clusters<IN_BF16, float, 128, false>(c.stages, k)
+                 : xs_max_clusters<IN_BF16, __nv_bfloat16, 128, false>(c.stages, k);
     slot = n > 0 ? n : -1;
   }
   return slot > 0 ? slot : 0;
 }
 
 // Whether plan `pl` of config `c` can run as a cluster split here: a
-// single-problem launch, eligible (xs_eligible), and one co-resident
-// cluster per tile.
-bool xs_runnable(const PlanOut &pl, const Cfg &c, const std::vector<Norm> &work, bool single, int dev, int sms) {
-  return single && xs_eligible(pl, c) && xs_capacity(dev, c, work[0].c_type == SK_F32, sms) >= pl.s.total_tiles;
+// single-problem launch, eligible (xs_units_per_tile), and, where the
+// library chooses it (one_wave), one co-resident cluster per tile so the
+// plan runs in one wave.  (Clusters never wait on one another, so an
+// explicit request runs correctly in several waves too.)
+bool xs_runnable(const PlanOut &pl, const Cfg &c, const std::vector<Norm> &work, bool single, int dev, int sms,
+                 bool one_wave) {
+  const int k = xs_units_per_tile(pl, c, work);
+  return single && k > 0 &&
+         (!one_wave || xs_capacity(dev, c, work[0].c_type == SK_F32, sms, k) >= pl.s.total_tiles);
 }
 
 sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vector<int> &idx, int sms, int dev,
@@ -1023,9 +1055,9 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
           last_rc = fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
           continue;
         }
-        if (c.fixup == FIXUP_SPLIT_CLUSTER && !xs_runnable(pl, c, work, single, dev, sms)) {
+        if (c.fixup == FIXUP_SPLIT_CLUSTER && !xs_runnable(pl, c, work, single, dev, sms, false)) {
           last_rc = fail_msg(SK_ERR_UNSUPPORTED,
-                             "cluster split: one BF16 problem, two tile-aligned units per tile, one cluster per tile");
+                             "cluster split: one BF16 or 3xTF32 problem, 2, 4 or 8 tile-aligned units per tile (at most 8 CTAs)");
           continue;
         }
         double ns = predict_ns(work, pl, c);
@@ -1073,7 +1105,12 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
               t3.fixup = fx;
               Cfg c3;
               if (resolve_cfg(fam, &t3, sms, &c3) != SK_OK) continue;
-              if (fx == SK_FIXUP_SPLIT_CLUSTER && !xs_runnable(pl2, c3, work, single, dev, sms)) continue;
+              // (the library picks the cluster split with two units per tile
+              // only: with 4 or 8 it measured no faster than the split reduce
+              // through the workspace)
+              if (fx == SK_FIXUP_SPLIT_CLUSTER &&
+                  (pl2.s.g != 2 * pl2.s.total_tiles || !xs_runnable(pl2, c3, work, single, dev, sms, true)))
+                continue;
               const double ns3 = predict_ns(work, pl2, c3);
               if (ns3 < best * 0.999) {
                 best = ns3;
@@ -1101,6 +1138,8 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
                   try_units((int)(kk * T), false);
                   break;
                 }
+            // the cluster split with two units per tile
+            if (2 * T <= c.g && 2 * T != g_alt) try_units((int)(2 * T), true);
           }
         }
       }
@@ -1253,9 +1292,9 @@ sk_status run(const sk_problem *problems, int count, const sk_config *cfg, void 
   build_plan(work, idx, c, &pl);
   if (c.fixup == FIXUP_SPLIT && !split_eligible(pl))
     return fail_msg(SK_ERR_UNSUPPORTED, "split reduce: every unit must hold one tile-aligned range");
-  if (c.fixup == FIXUP_SPLIT_CLUSTER && !xs_runnable(pl, c, work, !grouped, dev, di.sms))
+  if (c.fixup == FIXUP_SPLIT_CLUSTER && !xs_runnable(pl, c, work, !grouped, dev, di.sms, false))
     return fail_msg(SK_ERR_UNSUPPORTED,
-                    "cluster split: one BF16 problem, two tile-aligned units per tile, one cluster per tile");
+                    "cluster split: one BF16 or 3xTF32 problem, 2, 4 or 8 tile-aligned units per tile (at most 8 CTAs)");
   Workspace w = carve(ws, c);
   void *table = static_cast<uint8_t *>(ws) + ws_base_bytes(c);   // used for groups beyond MAXP_GROUPED
   if (c.fam == FAM_F32 && !c.tc32) {
@@ -1288,7 +1327,7 @@ sk_status plan_for_query(const sk_problem *problems, int count, const sk_config 
   }
   build_plan(work, idx, *c, pl);
   if (c->fixup == FIXUP_SPLIT && !work.empty() && !split_eligible(*pl)) return SK_ERR_UNSUPPORTED;
-  if (c->fixup == FIXUP_SPLIT_CLUSTER && !work.empty() && !xs_runnable(*pl, *c, work, count == 1, dev, sms))
+  if (c->fixup == FIXUP_SPLIT_CLUSTER && !work.empty() && !xs_runnable(*pl, *c, work, count == 1, dev, sms, false))
     return SK_ERR_UNSUPPORTED;
   pl->predicted_ns = work.empty() ? 0.0 : predict_ns(work, *pl, *c);
   return SK_OK;

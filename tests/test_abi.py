@@ -285,13 +285,14 @@ def test_library_split_choice_is_eligible(sk, shape):
 
 def test_fault_injection_keeps_the_owner_protocol(sk):
     """With the test-only injection set (peers withhold their flags), the
-    library never picks the split reduce by itself, and the decision cache
-    keeps the two requests apart."""
+    library never picks the split reduce (through the workspace or the
+    cluster) by itself, and the decision cache keeps the two requests apart."""
     B = sk.binding
     p = sk.shape_problem(384, 384, 2048, dtype="f32")
-    assert sk.plan(p, num_sms=152).fixup == B.SK_FIXUP_SPLIT
+    split = (B.SK_FIXUP_SPLIT, B.SK_FIXUP_SPLIT_CLUSTER)
+    assert sk.plan(p, num_sms=152).fixup in split
     assert sk.plan(p, sk.Config(debug_flags=1), num_sms=152).fixup == B.SK_FIXUP_OWNER
-    assert sk.plan(p, num_sms=152).fixup == B.SK_FIXUP_SPLIT
+    assert sk.plan(p, num_sms=152).fixup in split
 
 
 def test_f32_kernel_choice(sk):
@@ -488,9 +489,11 @@ def test_coverage_words(sk):
 
 
 def test_cluster_split_eligibility(sk):
-    """SK_FIXUP_SPLIT_CLUSTER runs only where every tile has exactly two
-    tile-aligned units, on one BF16 problem, with 128-row tiles or 256 x 256
-    pairs; elsewhere the request is SK_ERR_UNSUPPORTED."""
+    """SK_FIXUP_SPLIT_CLUSTER runs only where every tile has 2, 4 or 8
+    tile-aligned units (at most 8 CTAs per cluster), on one BF16 or 3xTF32
+    problem, with 128-row tiles or 256 x 256 pairs, and where the operand
+    ring holds the exchanged blocks; elsewhere the request is
+    SK_ERR_UNSUPPORTED."""
     B = sk.binding
 
     def q(shape, cfg, dtype="bf16", count=1):
@@ -501,16 +504,24 @@ def test_cluster_split_eligibility(sk):
         return B.sk_plan_query(arr, count, ctypes.byref(c), 152, ctypes.byref(info)), info
 
     xs = {"mode": "sk", "fixup": "split_cluster"}
-    # 36 tiles of 256 x 256 on 72 pairs, 64 k-blocks each: eligible
-    rc, info = q((1536, 1536, 8192), {**xs, "tile_m": 256, "num_ctas": 144})
-    assert rc == B.SK_OK and info.fixup == B.SK_FIXUP_SPLIT_CLUSTER and info.num_ctas == 2 * info.tiles
-    # 64 tiles of 128 x 128 on 128 CTAs
-    rc, info = q((128, 8192, 16384), {**xs, "tile_m": 128, "tile_n": 128, "num_ctas": 128})
-    assert rc == B.SK_OK and info.fixup == B.SK_FIXUP_SPLIT_CLUSTER
-    # not two units per tile, three units per tile, FP32, E4M3, 256 x 128 pairs, two problems
+    for shape, cfg, dt, k in [
+            ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 144}, "bf16", 2),   # 36 tiles, 72 pairs
+            ((512, 512, 8192), {"tile_m": 256, "num_ctas": 32}, "bf16", 4),     # 4 tiles, 16 pairs
+            ((128, 8192, 16384), {"tile_m": 128, "tile_n": 128, "num_ctas": 128}, "bf16", 2),
+            ((512, 512, 8192), {"tile_m": 128, "tile_n": 128, "num_ctas": 64}, "bf16", 4),
+            ((512, 512, 8192), {"tile_m": 128, "tile_n": 128, "num_ctas": 128}, "bf16", 8),
+            ((384, 384, 2048), {"tile_m": 128, "num_ctas": 72}, "f32", 8),        # 3xTF32, 9 tiles
+            ((1024, 1024, 4096), {"tile_m": 256, "num_ctas": 128}, "f32", 4)]:   # 3xTF32 pairs
+        rc, info = q(shape, {**xs, **cfg}, dtype=dt)
+        assert rc == B.SK_OK and info.fixup == B.SK_FIXUP_SPLIT_CLUSTER, (shape, cfg)
+        assert info.num_ctas == k * info.tiles, (shape, cfg)
+    # not k units per tile, three units per tile, 8 pairs per tile (16 CTAs),
+    # BF16 output with 8 units of 128 x 256 (the ring misses the blocks), the
+    # FFMA kernel, E4M3, 256 x 128 pairs, two problems
     for shape, cfg, dt, cnt in [((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 152}, "bf16", 1),
                                 ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 108}, "bf16", 1),
-                                ((384, 384, 2048), {"tile_m": 128, "num_ctas": 18}, "f32", 1),
+                                ((512, 512, 8192), {"tile_m": 256, "num_ctas": 64}, "bf16", 1),
+                                ((384, 384, 2048), {"tile_m": 128, "num_ctas": 18, "f32_kernel": "ffma"}, "f32", 1),
                                 ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 144}, "e4m3", 1),
                                 ((1536, 1536, 8192), {"tile_m": 256, "tile_n": 128, "num_ctas": 144}, "bf16", 1),
                                 ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 144}, "bf16", 2)]:

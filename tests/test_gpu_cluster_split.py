@@ -1,11 +1,11 @@
 """GPU parity of the cluster split (SK_FIXUP_SPLIT_CLUSTER).
 
-Each tile is cut into two tile-aligned Stream-K ranges; the two units run as
-one thread-block cluster and exchange, through distributed shared memory,
-the halves of their partial accumulators that the other sums.  C must be
-bit-identical to the owner protocol on the same plan (the partial of the
-unit holding k-block 0 plus the other partial: one addition), within the
-oracle's bound, and the same from run to run.
+Each tile is cut into k = 2, 4 or 8 tile-aligned Stream-K ranges; the k
+units run as one thread-block cluster and exchange, through distributed
+shared memory, the blocks of their partial accumulators that the others
+sum.  C must be bit-identical to the owner protocol on the same plan (the
+partials added in ascending unit order), within the oracle's bound, and
+the same from run to run.
 """
 import numpy as np
 import pytest
@@ -29,26 +29,31 @@ def _inputs(M, N, K, seed, dist="uniform"):
 
 
 CASES = [
-    # shape, tile (m, n), CTAs: two units per tile
-    ((1536, 1536, 8192), (256, 256), 144),
-    ((512, 512, 2048), (256, 256), 16),
-    ((700, 900, 1024), (256, 256), 48),      # ragged M and N
-    ((128, 8192, 16384), (128, 128), 128),
-    ((300, 520, 768), (128, 128), 30),       # ragged
-    ((600, 1000, 2048), (128, 256), 40),
+    # shape, tile (m, n), CTAs, units per tile
+    ((1536, 1536, 8192), (256, 256), 144, 2),
+    ((512, 512, 2048), (256, 256), 16, 2),
+    ((700, 900, 1024), (256, 256), 48, 2),      # ragged M and N
+    ((128, 8192, 16384), (128, 128), 128, 2),
+    ((300, 520, 768), (128, 128), 30, 2),       # ragged
+    ((600, 1000, 2048), (128, 256), 40, 2),
+    ((512, 512, 8192), (256, 256), 32, 4),      # clusters of 8 CTAs (4 pairs)
+    ((512, 512, 8192), (128, 128), 64, 4),
+    ((512, 512, 8192), (128, 128), 128, 8),
+    ((300, 520, 1024), (128, 128), 120, 8),     # ragged, 2 k-blocks per unit
+    ((640, 384, 2048), (128, 256), 40, 4),
 ]
 
 
 @pytest.mark.parametrize("out_dtype", [torch.bfloat16, torch.float32])
-@pytest.mark.parametrize("shape,tile,ctas", CASES)
-def test_cluster_split_equals_owner(m, shape, tile, ctas, out_dtype):
+@pytest.mark.parametrize("shape,tile,ctas,k", CASES)
+def test_cluster_split_equals_owner(m, shape, tile, ctas, k, out_dtype):
     M, N, K = shape
     a, b = _inputs(M, N, K, seed=M + N + K)
     base = dict(mode="sk", tile_m=tile[0], tile_n=tile[1], num_ctas=ctas, min_iters_per_unit=1)
     info = m.plan(m.make_problem(a, b, torch.empty(M, N, dtype=out_dtype, device=a.device)),
                   m.Config(**base, fixup="split_cluster"))
     assert info.fixup == m.binding.SK_FIXUP_SPLIT_CLUSTER
-    assert info.num_ctas == 2 * info.tiles
+    assert info.num_ctas == k * info.tiles
     c_xs = m.gemm(a, b, config=m.Config(**base, fixup="split_cluster"), out_dtype=out_dtype)
     assert m.default_workspace(dev()).status() == 0
     c_own = m.gemm(a, b, config=m.Config(**base, fixup="owner"), out_dtype=out_dtype)
@@ -99,3 +104,27 @@ def test_library_picks_cluster_split(m, shape):
     cfg = dict(mode=["auto", "dp", "sk", "hybrid1", "hybrid2"][info.mode], tile_m=info.tile_m,
                tile_n=info.tile_n, num_ctas=info.num_ctas * (2 if info.tile_m == 256 else 1))
     assert torch.equal(c, m.gemm(a, b, config=m.Config(**cfg, fixup="owner")))
+
+
+@pytest.mark.parametrize("shape,tile,ctas,k", [((384, 384, 2048), (128, 128), 18, 2),
+                                               ((384, 384, 2048), (128, 128), 36, 4),
+                                               ((384, 384, 2048), (128, 128), 72, 8),
+                                               ((1024, 1024, 4096), (256, 256), 128, 4),
+                                               ((520, 390, 1024), (128, 128), 80, 4)])
+def test_cluster_split_3xtf32(m, shape, tile, ctas, k):
+    """FP32 problems on the tensor cores (3xTF32): the cluster split equals
+    the owner protocol bit for bit and meets the FP32 bound."""
+    M, N, K = shape
+    a, b = workloads.gemm_inputs(M, N, K, dtype="f32", seed=M + K)
+    d = dev()
+    a, b = same_strides(a, d), same_strides(b, d)
+    base = dict(mode="sk", tile_m=tile[0], tile_n=tile[1], num_ctas=ctas, min_iters_per_unit=1,
+                f32_kernel="tf32x3")
+    info = m.plan(m.make_problem(a, b, torch.empty(M, N, dtype=torch.float32, device=d)),
+                  m.Config(**base, fixup="split_cluster"))
+    assert info.fixup == m.binding.SK_FIXUP_SPLIT_CLUSTER and info.num_ctas == k * info.tiles
+    c_xs = m.gemm(a, b, config=m.Config(**base, fixup="split_cluster"))
+    assert m.default_workspace(d).status() == 0
+    c_own = m.gemm(a, b, config=m.Config(**base, fixup="owner"))
+    assert torch.equal(c_xs, c_own)
+    assert_within_bound(c_xs, a.cpu(), b.cpu(), out="f32", what="cluster split 3xTF32")

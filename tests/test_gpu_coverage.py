@@ -136,7 +136,10 @@ def test_coverage_split_reduce(m, shape, tile, ctas):
 
 @pytest.mark.parametrize("shape,tile,ctas", [((384, 384, 2048), (128, 128), 18),
                                              ((700, 900, 1024), (128, 256), 48),
-                                             ((1536, 1536, 8192), (256, 256), 144)])
+                                             ((1536, 1536, 8192), (256, 256), 144),
+                                             ((512, 512, 8192), (256, 256), 32),
+                                             ((384, 384, 2048), (128, 128), 72),
+                                             ((640, 384, 2048), (128, 256), 40)])
 def test_coverage_cluster_split(m, shape, tile, ctas):
     cfg = m.Config(mode="sk", tile_m=tile[0], tile_n=tile[1], num_ctas=ctas, fixup="split_cluster",
                    min_iters_per_unit=1)

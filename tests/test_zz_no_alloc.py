@@ -126,8 +126,9 @@ def test_static_ws_size_limits():
     ad, bd = a.to(d), b.to(d)
     c = torch.empty(256, 512, dtype=torch.bfloat16, device=d)
     p = m.make_problem(ad, bd, c)
-    cfg = B.sk_config()
-    cfg.tile_n = 256                  # 128 KB of partials per CTA on every SM: > 12 MiB
+    # 128x256 tiles, Stream-K on every SM with the owner fixup: 128 KB of
+    # partials per CTA, > 12 MiB
+    cfg = m.Config(mode="sk", tile_m=128, tile_n=256, num_ctas=sms).to_c()
     assert B.sk_gemm_static_ws(ctypes.byref(p), ctypes.byref(cfg), _stream()) == B.SK_ERR_WORKSPACE_TOO_SMALL
     la = m.Config(mode="sk", tile_m=128, tile_n=128, fixup="last_arriver").to_c()
     assert B.sk_gemm_static_ws(ctypes.byref(p), ctypes.byref(la), _stream()) == B.SK_ERR_WORKSPACE_TOO_SMALL
