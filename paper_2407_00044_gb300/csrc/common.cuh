@@ -118,6 +118,10 @@ struct TcParams {
   int32_t xs_k;         // FIXUP_SPLIT_CLUSTER: units per tile (= per cluster), 2, 4 or 8
 };
 
+// Cluster split: most units a contributor sums (NS / k with NS <= 32 and
+// k >= 2), one data barrier each.
+constexpr int XS_MAX_UNITS = 16;
+
 // Coverage word increment of one visit by unit u (SK_COVERAGE_VISIT).
 __host__ __device__ __forceinline__ uint32_t cover_visit(int u) { return 1u + ((uint32_t)(u + 1) << 8); }
 

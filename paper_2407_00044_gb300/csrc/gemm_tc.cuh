@@ -184,8 +184,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   uint64_t *fix_bar = done_bar + 1;   // FIX_SMEM_UNITS barriers of the staged fixup
   uint64_t *conv_bar = fix_bar + FIX_SMEM_UNITS;   // 3xTF32: stage split (one per stage; the leader's in a pair)
   uint64_t *xr_bar = conv_bar + (X3 ? stages : 0);   // XS: the partner's ring is free to write
-  uint64_t *xd_bar = xr_bar + 1;                      // XS: every partner's blocks have arrived
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + 1);
+  uint64_t *xd_bar = xr_bar + 1;                      // XS: per own unit, every partner's block has arrived
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xd_bar + (XS ? XS_MAX_UNITS : 0));
   volatile uint32_t *abort_flag = tmem_slot + 1;
   volatile uint32_t *fix_word = tmem_slot + 2;   // two words: last-arriver decisions
   volatile uint32_t *fix_fail = tmem_slot + 4;   // two words: a staged-sum group failed
@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
     for (int b = 0; b < FIX_SMEM_UNITS; ++b) mbar_init(smem_u32(fix_bar + b), 1);
     if constexpr (XS) {
       mbar_init(smem_u32(xr_bar), (uint32_t)(P.xs_k - 1));   // one remote arrival per partner
-      mbar_init(smem_u32(xd_bar), 1);                        // this CTA's arrive.expect_tx
+      for (int l = 0; l < XS_MAX_UNITS; ++l) mbar_init(smem_u32(xd_bar + l), 1);   // this CTA's arrive.expect_tx
     }
     if constexpr (X3)   // the 4 epilogue warps of this CTA (of both CTAs in a pair)
       for (int s = 0; s < stages; ++s) mbar_init(smem_u32(conv_bar + s), PAIR ? 8 : 4);
@@ -828,7 +828,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         // the other contributors' units in unit order]
         const uint32_t out_base = (uint32_t)((kc - 1) * own_n) * BLK;
         if (et == 0) {
-          mbar_arrive_expect_tx(smem_u32(xd_bar), out_base);   // incoming bytes
+          // one barrier per own unit: its kc - 1 incoming blocks
+          for (int l = 0; l < own_n; ++l) mbar_arrive_expect_tx(smem_u32(xd_bar + l), (uint32_t)(kc - 1) * BLK);
           for (int i = 0; i < kc; ++i)
             if (i != jx) mbar_arrive_cluster(mapa_shared(smem_u32(xr_bar), cta_of(i)));   // this ring is free
         }
@@ -860,15 +861,18 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             __syncwarp();
             if (lane == 0)
               bulk_copy_s2cluster(mapa_shared(tiles_addr + dst_off, cta_of(i)), tiles_addr + stg_off, BLK,
-                                  mapa_shared(smem_u32(xd_bar), cta_of(i)));
+                                  mapa_shared(smem_u32(xd_bar + (s - s_lo(i))), cta_of(i)));
           }
           if (tr_lead) trace_put(trace, TRACE_FIX_BASE + 5, 15, nitem, globaltimer_ordered());   // blocks sent
-          okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar), 0u, tmo));
-          if (!okx && lane == 0) fail();
-          if (tr_lead && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
           const float alpha = get_alpha();
+          bool first = true;
 #pragma unroll 1
           for (int s = s0 + ((q4 - s0 % 4) + 4) % 4; s < s1; s += 4) {   // this warp's own units
+            // summed as soon as the unit's blocks have landed
+            okx = __all_sync(0xffffffffu, mbar_wait_cluster(smem_u32(xd_bar + (s - s0)), 0u, tmo));
+            if (!okx && lane == 0) fail();
+            if (tr_lead && first && nitem < 21) trace_put(trace, tr + 1, 6, nitem, globaltimer_ordered());
+            first = false;
 #pragma unroll
             for (int h = 0; h < UW; ++h) {
               float v[32];

@@ -474,6 +474,7 @@ int xs_units_per_tile(const PlanOut &pl, const Cfg &c, const std::vector<Norm> &
   const int ns = 4 * (c.BN / 32) / uw;
   const int blk = uw * 4096;
   const int own_max = (ns + k - 1) / k, own_min = ns / k;
+  if (own_max > XS_MAX_UNITS) return 0;   // one data barrier per own unit
   const int stage = (128 * 128 + (c.pair ? c.BN / 2 : c.BN) * 128) * (c.tc32 ? 2 : 1);
   if ((int64_t)c.stages * stage < (int64_t)((k - 1) * own_max + (ns - own_min)) * blk) return 0;
   return k;
