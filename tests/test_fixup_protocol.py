@@ -250,3 +250,101 @@ def test_split_units_cover_the_tile_once(bn, f32_out, kc):
     if not f32_out:
         for (ch, q4), j in owner.items():
             assert owner[(ch ^ 1, q4)] == j
+
+
+# ---- cluster split ----------------------------------------------------------
+# The kc contributors of a tile form one cluster.  Each, once its MMAs are
+# done (its operand ring is free), arms one data barrier per unit it sums
+# (expecting kc - 1 blocks) and arrives on every partner's ring-free
+# barrier; after all kc - 1 partners have arrived it sends each unit that
+# another contributor sums as one block into that contributor's ring
+# (counted on the receiver's barrier of that unit); it sums a unit of its
+# own once that unit's barrier has seen kc - 1 blocks.  Checked over every
+# interleaving: a block lands only in a ring that is free, every sum reads
+# kc - 1 landed blocks, and every contributor finishes (no deadlock).
+
+def _xs_layout(ns, kc):
+    """Units each contributor sums (the split reduce's dealing)."""
+    return [list(range(j * ns // kc, (j + 1) * ns // kc)) for j in range(kc)]
+
+
+def _xs_explore(kc, ns):
+    owned = _xs_layout(ns, kc)
+    owner_of = {s: j for j in range(kc) for s in owned[j]}
+    # per contributor: armed, ring-free arrivals received, blocks received
+    # per own unit, sends done, sums done
+    seen, terminals = set(), set()
+
+    def steps(j):
+        out = [("free", None)]
+        out += [("send", s) for s in range(ns) if owner_of[s] != j]
+        out += [("sum", s) for s in owned[j]]
+        return out
+
+    progs = [steps(j) for j in range(kc)]
+
+    def go(pc, free, arrivals, landed):
+        key = (pc, free, arrivals, landed)
+        if key in seen:
+            return
+        seen.add(key)
+        moved = False
+        for j in range(kc):
+            if pc[j] == len(progs[j]):
+                continue
+            op, s = progs[j][pc[j]]
+            fr, ar, la = set(free), list(arrivals), dict(landed)
+            if op == "free":
+                fr.add(j)                    # MMAs done: ring free, barriers armed
+                for i in range(kc):
+                    if i != j:
+                        ar[i] += 1           # remote arrival on i's ring-free barrier
+            elif op == "send":
+                if ar[j] < kc - 1:
+                    continue                 # blocked until every partner's ring is free
+                dst = owner_of[s]
+                assert dst in fr, "a block written into a busy ring"
+                la[s] = la.get(s, 0) + 1
+            elif op == "sum":
+                if la.get(s, 0) < kc - 1:
+                    continue                 # blocked on the unit's barrier
+                assert la[s] == kc - 1
+            moved = True
+            go(pc[:j] + (pc[j] + 1,) + pc[j + 1:], frozenset(fr), tuple(ar), tuple(sorted(la.items())))
+        if not moved:
+            assert all(pc[j] == len(progs[j]) for j in range(kc)), "deadlock"
+            terminals.add(key)
+
+    go(tuple([0] * kc), frozenset(), tuple([0] * kc), ())
+    return len(terminals)
+
+
+@pytest.mark.parametrize("kc,ns", [(2, 4), (2, 8), (4, 4), (4, 8), (3, 5)])
+def test_cluster_split_every_interleaving(kc, ns):
+    assert _xs_explore(kc, ns) > 0
+
+
+@pytest.mark.parametrize("bn,f32_out", [(128, True), (128, False), (256, True), (256, False)])
+@pytest.mark.parametrize("kc", [2, 4, 8])
+def test_cluster_split_blocks_fit(bn, f32_out, kc):
+    """Ring layout of the cluster split: each contributor's incoming slots
+    (source, own unit) and the senders' destination offsets are a bijection
+    onto [0, (kc - 1) x own units) blocks, and every contributor's outgoing
+    staging indexes the other contributors' units once."""
+    uw = 1 if f32_out else 2
+    ns = 4 * (bn // 32) // uw
+    if ns < kc:
+        return
+    lo = [j * ns // kc for j in range(kc + 1)]
+    for j in range(kc):                      # receiver
+        own_n = lo[j + 1] - lo[j]
+        slots = set()
+        for i in range(kc):                  # sender
+            if i == j:
+                continue
+            src_slot = i if i < j else i - 1
+            for s in range(lo[j], lo[j + 1]):
+                slots.add(src_slot * own_n + (s - lo[j]))
+        assert slots == set(range((kc - 1) * own_n))
+        stg = [s - (own_n if s >= lo[j + 1] else 0) for s in range(ns) if not lo[j] <= s < lo[j + 1]]
+        assert sorted(stg) == list(range(ns - own_n))
