@@ -332,7 +332,7 @@ def run_ours(args, world, rank, local):
                 "frac": round(achieved / pk["bf16"], 4),
                 # the committed capture is of the 8192^3 launch
                 "traffic": profiled_traffic() if shapes[di] == DOMINANT_SHAPE else None,
-                "kernel": "sk_tc_kernel<bf16,bf16,BN=256,pair> on %dx%dx%d" % shapes[di],
+                "kernel": "sk_tc_kernel<bf16,bf16,%s tile> on %dx%dx%d" % ((per_shape[di]["tile"],) + shapes[di]),
                 "peak_source": f"{pk['source']} bf16 burst (the launch is timed alone)",
                 # context: the same against the seconds-long sustained figure
                 "frac_of_sustained": round(achieved / pk["bf16_sustained"], 4),

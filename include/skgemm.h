@@ -170,8 +170,11 @@ typedef struct {
                                 share one 256 x tile_n tile through tcgen05
                                 cta_group::2; BF16 and E4M3); 0 = chosen by the
                                 library's runtime model */
-    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256 (pair: 256, or 128 for
-                                BF16); 0 = chosen by the library's runtime model */
+    int tile_n;              /* F32: 128; BF16/E4M3: 128 or 256; pair: 256, 128 (BF16)
+                                or 512 (BF16/E4M3, one problem: two N = 256 MMAs per
+                                k-step into one 512-column TMEM accumulator, no
+                                epilogue overlap); 0 = chosen by the library's
+                                runtime model (512 only for data-parallel plans) */
     int stages;              /* smem pipeline depth (BF16/E4M3: 2..6; default by tile) */
     sk_mode mode;            /* decomposition; default AUTO */
     int num_ctas;            /* persistent CTAs, 1 <= num_ctas <= SM count; 0 = SM count,

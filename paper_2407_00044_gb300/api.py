@@ -122,9 +122,10 @@ def make_problem(A: torch.Tensor, Bm: torch.Tensor, C: torch.Tensor, *, C_in=Non
 
 def default_workspace_bytes(sms: int) -> int:
     """Workspace for any call on a GPU with ``sms`` SMs: status word (256 B),
-    the fixed flag region (1024 words), and two 128 x 256 FP32 slots per CTA
-    (the second is used by the last-arriver fixup only)."""
-    return 256 + 4096 + 2 * sms * 128 * 256 * 4
+    the fixed flag region (1024 words), and two 128 x 512 FP32 slots per CTA
+    (a CTA's share of the widest tile, 256 x 512 on a CTA pair; the second
+    slot is used by the last-arriver fixup only)."""
+    return 256 + 4096 + 2 * sms * 128 * 512 * 4
 
 
 class Workspace:

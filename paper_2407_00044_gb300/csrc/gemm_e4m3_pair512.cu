@@ -1,0 +1,10 @@
+// FP8 E4M3-input instantiations of the CTA-pair Stream-K kernel with
+// 256 x 512 tiles (single problem, K-major operands).
+#include "gemm_tc.cuh"
+
+namespace sk {
+template cudaError_t launch_tc<IN_E4M3, __nv_bfloat16, 512, 1, true>(const TcParams<1> &, int, cudaStream_t);
+template cudaError_t launch_tc<IN_E4M3, float, 512, 1, true>(const TcParams<1> &, int, cudaStream_t);
+template int pair_max_clusters<IN_E4M3, __nv_bfloat16, 512, 1>(int);
+template int pair_max_clusters<IN_E4M3, float, 512, 1>(int);
+}  // namespace sk

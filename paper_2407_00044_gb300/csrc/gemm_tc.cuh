@@ -126,6 +126,11 @@ struct OutStore<__nv_bfloat16> {
 };
 
 // PAIR = false: one CTA per unit, 128 x BN tile, tcgen05 cta_group::1.
+// BN = 512 (pairs, BF16 / E4M3): two N = 256 MMAs per k-step into one
+//   512-column accumulator -- all of TMEM, so the epilogue of a tile is not
+//   overlapped by the next tile's MMAs -- with a quarter fewer shared-memory
+//   bytes (TMA writes + MMA operand reads) per MAC than a 256 x 256 pair.
+//   Each CTA holds B rows [r*128, r*128+128) of either MMA's 256 columns.
 // PAIR = true : a cluster of two CTAs per unit, 256 x BN tile.  Each CTA
 //   TMA-loads its own 128 rows of A and its half (BN/2 rows) of B (either
 //   operand K-major or MN-major) into its
@@ -162,10 +167,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
   // both halves there).
   constexpr bool OWN_FULL = !PAIR || X3;
   constexpr int TX_BYTES = OWN_FULL ? OP_BYTES : 2 * OP_BYTES;
-  constexpr uint32_t TMEM_COLS = 2 * BN;
+  constexpr int MMA_N = BN > 256 ? 256 : BN;   // columns per MMA
+  constexpr int NMMA = BN / MMA_N;               // MMAs per k-step (BN = 512: 2)
+  constexpr int NACC = BN > 256 ? 1 : 2;         // TMEM accumulators (double-buffered up to BN = 256)
+  constexpr int B_BLOCK = B_ROWS / NMMA;         // B rows of one MMA in this CTA
+  constexpr uint32_t TMEM_COLS = NACC * BN;
   constexpr int MN_CHUNK_BYTES = BK * 128;   // one 64-wide MN chunk of an MN-major slice
-  constexpr uint32_t IDESC = Tr::IDESC_TYPES | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "tile N");
+  constexpr uint32_t IDESC = Tr::IDESC_TYPES | ((uint32_t)(MMA_N >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(BN % 32 == 0 && BN >= 32 && (BN <= 256 || (BN == 512 && PAIR && !XS)), "tile N");
+  static_assert(BN <= 256 || IN != IN_TF32X3, "512-column tiles: BF16 and E4M3 pairs");
   static_assert(!PAIR || BN % 64 == 0, "pair tile N");
   static_assert(!X3 || !PAIR || BN == 256, "3xTF32 pairs use 256 x 256 tiles");
 
@@ -284,7 +294,8 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           acquired = w.problem;
         }
         const int m0 = w.tm * BM + (int)rank * 128;
-        const int n0 = w.tn * BN + (int)rank * B_ROWS;
+        // B rows of MMA j: n0 + j * MMA_N (+ 64 * chunk for MN-major loads)
+        const int n0 = w.tn * BN + (int)rank * B_BLOCK;
         // Both operands K-major is the common case: one load per operand,
         // decided once per item (a per-load layout test in the pair loop
         // measured 16 % slower on 8192^3).
@@ -303,7 +314,9 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
             const uint32_t fbl = mapa_shared(fb, pbase);   // the leader's barrier
             if (kmaj) {
               tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
-              tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
+#pragma unroll
+              for (int j = 0; j < NMMA; ++j)
+                tma_load_2d_pair(sb + j * B_BLOCK * 128, &pr.tmap_b, fbl, kx, n0 + j * MMA_N);
             } else {
               if (!pr.a_mn) {
                 tma_load_2d_pair(sa, &pr.tmap_a, fbl, kx, m0);
@@ -313,11 +326,15 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                   tma_load_2d_pair(sa + ch * MN_CHUNK_BYTES, &pr.tmap_a, fbl, m0 + 64 * ch, kx);
               }
               if (!pr.b_mn) {
-                tma_load_2d_pair(sb, &pr.tmap_b, fbl, kx, n0);
+#pragma unroll
+                for (int j = 0; j < NMMA; ++j)
+                  tma_load_2d_pair(sb + j * B_BLOCK * 128, &pr.tmap_b, fbl, kx, n0 + j * MMA_N);
               } else {
+                constexpr int CPM = B_BLOCK / 64;   // 64-wide chunks per MMA block
 #pragma unroll
                 for (int ch = 0; ch < B_ROWS / 64; ++ch)
-                  tma_load_2d_pair(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fbl, n0 + 64 * ch, kx);
+                  tma_load_2d_pair(sb + ch * MN_CHUNK_BYTES, &pr.tmap_b, fbl, n0 + (ch / CPM) * MMA_N + 64 * (ch % CPM),
+                                   kx);
               }
             }
           } else {
@@ -437,10 +454,16 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
                 mma_tf32(d_tmem, ad + LO, bd, idesc, 1u);
               }
             } else if constexpr (PAIR) {
-              if constexpr (IN == IN_BF16)
-                mma_f16_pair(d_tmem, ad, bd, idesc, accum);
-              else
-                mma_f8_pair(d_tmem, ad, bd, idesc, accum);
+              // (BN = 512: MMA j reads this CTA's B block j, B_BLOCK rows on,
+              // and writes accumulator columns [j * 256, j * 256 + 256))
+#pragma unroll
+              for (int j = 0; j < NMMA; ++j) {
+                const uint64_t bdj = bd + (uint64_t)((j * B_BLOCK * 128) >> 4);
+                if constexpr (IN == IN_BF16)
+                  mma_f16_pair(d_tmem + j * MMA_N, ad, bdj, idesc, accum);
+                else
+                  mma_f8_pair(d_tmem + j * MMA_N, ad, bdj, idesc, accum);
+              }
             } else {
               if constexpr (IN == IN_BF16)
                 mma_f16(d_tmem, ad, bd, idesc, accum);
@@ -469,7 +492,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
           mma_commit(smem_u32(tfull_bar + acc));
         if (DBG && nitem < 16) trace_put(trace, tr + 2, 4, nitem, globaltimer());
         ++nitem;
-        if (++acc == 2) {
+        if (++acc == NACC) {
           acc = 0;
           acc_phase ^= 1u;
         }
@@ -1185,7 +1208,7 @@ __global__ void __launch_bounds__(192, 1) sk_tc_kernel(const __grid_constant__ T
         if (tr_lead && nitem < 21) trace_put(trace, tr + 2, 7, nitem, globaltimer_ordered());
       }
       ++nitem;
-      if (++acc == 2) {
+      if (++acc == NACC) {
         acc = 0;
         acc_phase ^= 1u;
       }

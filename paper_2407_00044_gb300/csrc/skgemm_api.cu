@@ -229,8 +229,8 @@ sk_status resolve_cfg(Family fam, const sk_config *c, int sms, Cfg *out) {
     r.stages = 2;
   } else {
     r.BN = d.tile_n ? d.tile_n : 256;
-    if (r.BN != 128 && r.BN != 256) return SK_ERR_UNSUPPORTED;
-    if (r.pair && r.BN != 256 && fam != FAM_BF16) return SK_ERR_UNSUPPORTED;   // 256 x 128 pairs: BF16
+    if (r.BN != 128 && r.BN != 256 && !(r.BN == 512 && r.pair)) return SK_ERR_UNSUPPORTED;   // 256 x 512: pairs
+    if (r.pair && r.BN == 128 && fam != FAM_BF16) return SK_ERR_UNSUPPORTED;   // 256 x 128 pairs: BF16
     r.BK = fam == FAM_BF16 ? 64 : 128;
     const int stage_bytes = 128 * 128 + (r.pair ? r.BN / 2 : r.BN) * 128;   // per CTA
     const int max_stages = std::min(8, (227 * 1024 - 1024 - 512 - EPI_STAGE_BYTES) / stage_bytes);
@@ -389,7 +389,8 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 //
 // Each unit is simulated as the kernel runs it: an MMA chain (k-blocks x
 // t_iter + t_mac_item per item) feeding an epilogue chain through two TMEM
-// accumulators, so item i's MMAs wait for the epilogue of item i-2.  The
+// accumulators, so item i's MMAs wait for the epilogue of item i-2 (i-1
+// for 256 x 512 pairs, whose one accumulator fills TMEM).  The
 // epilogue of an item costs
 //   whole / DP tile : t_store
 //   peer            : t_spill                      (and records when the
@@ -422,6 +423,18 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // model then ranks the two tiles as measured on all seven (pairs win from
 // 1024x1024x4096 up, e.g. 4096^3 505 against 643 us).
 #define TF32X3_PAIR_COEFFS 1100.0, 1190.0, 8500.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0
+// 256 x 512 pairs: a k-block (two N = 256 MMAs) measured 0.573 us against
+// 0.650 us for two 256 x 256 k-blocks (per-CTA timeline, 8192^3 DP, same
+// clock); TMEM holds one 512-column accumulator, so a tile's MMAs wait for
+// the previous tile's epilogue and for its last MMAs to drain.  A fit of
+// launch + items x (k-blocks x t_iter + t_item) to 14 DP shapes (K 1024 to
+// 16384, 1 to 27 tiles per pair) gave t_iter 560 ns, t_item 6.8 us and a
+// 7.9 us launch (2 % rms); the values below sit at the low edge of that fit
+// so that, against the 256 x 256 pair's coefficients, the model picks the
+// wide tile where it measured faster (8192^3, 8192 x 8192 x 16384,
+// 6144 x 6144 x 12288: 2-6 %) and not where it measured slower (K = 4096,
+// or more than ~10 tiles per pair).  Partials are twice a 256 x 256 pair's.
+#define PAIR512_COEFFS 550.0, 1500.0, 7920.0, 5000.0, 10060.0, 0.0, 6900.0, 8060.0
 
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)
@@ -433,12 +446,14 @@ struct ModelCoeffs {
   double fix_peer_last_ns;   // per peer partial, staged fixup (the CTA's last item)
   double fix_peer_mid_ns;    // per peer partial, plain fixup (more work follows)
   bool serial;               // epilogue on the same threads as the MMA chain
+  bool one_acc = false;      // one TMEM accumulator: an item's MMAs wait for the previous epilogue
 };
 
 ModelCoeffs model_coeffs(const Cfg &c) {
   if (c.fam == FAM_F32 && c.tc32) return c.pair ? ModelCoeffs{TF32X3_PAIR_COEFFS, false} : ModelCoeffs{TF32X3_COEFFS, false};
   if (c.fam == FAM_F32) return {1700.0, 500.0, 6000.0, 1000.0, 2000.0, 1000.0, 1000.0, 1000.0, true};
   if (c.pair && c.BN == 128) return {PAIR128_COEFFS, false};
+  if (c.pair && c.BN == 512) return {PAIR512_COEFFS, false, true};
   if (c.pair) return {302.0, 1190.0, 5270.0, 5510.0, 5030.0, 0.0, 3450.0, 4030.0, false};
   if (c.BN == 256) return {375.0, 760.0, 6520.0, 3030.0, 3920.0, 1760.0, 3320.0, 3790.0, false};
   return {284.0, 636.0, 5160.0, 3900.0, 3020.0, 0.0, 3210.0, 790.0, false};
@@ -603,7 +618,7 @@ double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c
       for (size_t i = 0; i < its.size(); ++i) {
         const Item &w = its[i];
         const bool last = i + 1 == its.size();
-        const double mac_start = k.serial ? epi_prev : std::max(mac_prev, epi_prev2);
+        const double mac_start = k.serial ? epi_prev : std::max(mac_prev, k.one_acc ? epi_prev : epi_prev2);
         const double mac_end = mac_start + (w.k1 - w.k0) * k.iter_ns * stretch + k.mac_item_ns;
         double start = std::max(mac_end, epi_prev);
         double e;
@@ -756,7 +771,9 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
     const bool b_k = n.b_layout == SK_COL_MAJOR;   // B(k,j) at B[k + j*ldb]
     rc = encode_operand(enc, &tp.tmap_a, n.A, n.in_type, a_k, n.M, n.K, n.lda, 128, c.BK);
     if (rc == SK_OK)
-      rc = encode_operand(enc, &tp.tmap_b, n.B, n.in_type, b_k, n.N, n.K, n.ldb, c.pair ? c.BN / 2 : c.BN, c.BK);
+      // (B rows per load: a pair CTA's half of one MMA's columns, at most 128)
+    rc = encode_operand(enc, &tp.tmap_b, n.B, n.in_type, b_k, n.N, n.K, n.ldb, c.pair ? std::min(c.BN / 2, 128) : c.BN,
+                        c.BK);
     if (rc != SK_OK) {
       delete P;
       return rc;
@@ -820,7 +837,13 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
   const bool f32out = probs[0].c_type == SK_F32;
   cudaError_t e = cudaErrorInvalidValue;
   if (c.fam == FAM_BF16) {
-    if (c.pair && c.BN == 256)
+    if (c.pair && c.BN == 512) {
+      if constexpr (MAXP == 1)
+        e = f32out ? launch_tc<IN_BF16, float, 512, 1, true>(*P, pl.grid, st)
+                   : launch_tc<IN_BF16, __nv_bfloat16, 512, 1, true>(*P, pl.grid, st);
+      else
+        e = cudaErrorNotSupported;
+    } else if (c.pair && c.BN == 256)
       e = f32out ? launch_tc<IN_BF16, float, 256, MAXP, true>(*P, pl.grid, st)
                  : launch_tc<IN_BF16, __nv_bfloat16, 256, MAXP, true>(*P, pl.grid, st);
     else if (c.pair)
@@ -837,7 +860,10 @@ sk_status launch_tc_family(const std::vector<Norm> &probs, const PlanOut &pl, co
                : launch_tc<IN_TF32X3, float, 128, MAXP, false>(*P, pl.grid, st);
   } else if (c.fam == FAM_E4M3) {
     if constexpr (MAXP == 1) {
-      if (c.pair)
+      if (c.pair && c.BN == 512)
+        e = f32out ? launch_tc<IN_E4M3, float, 512, 1, true>(*P, pl.grid, st)
+                   : launch_tc<IN_E4M3, __nv_bfloat16, 512, 1, true>(*P, pl.grid, st);
+      else if (c.pair)
         e = f32out ? launch_tc<IN_E4M3, float, 256, 1, true>(*P, pl.grid, st)
                    : launch_tc<IN_E4M3, __nv_bfloat16, 256, 1, true>(*P, pl.grid, st);
       else if (c.BN == 256)
@@ -1035,10 +1061,17 @@ sk_status choose_auto(Family fam, const std::vector<Norm> &work, const std::vect
     tns.clear();
     if (fam == FAM_F32) tns.push_back(d->tile_n);
     else if (!free_tile_n) tns.push_back(d->tile_n);
-    else if (tm == 256) tns.push_back(256);   // 256 x 128 pairs: only when asked for (never faster)
+    else if (tm == 256) {
+      tns.push_back(256);   // 256 x 128 pairs: only when asked for (never faster)
+      if (single && fam != FAM_F32) tns.push_back(512);
+    }
     else tns = {256, 128};
     for (int tn : tns) {
       for (sk_mode md : modes) {
+        // (the library picks 256 x 512 pairs for data-parallel plans only:
+        // their Stream-K partials are twice a 256 x 256 pair's and measured
+        // slower on every shape tried)
+        if (tn == 512 && free_tile_n && md != SK_MODE_DP) continue;
         sk_config t = *d;
         t.tile_m = tm;
         t.tile_n = tn;
@@ -1198,6 +1231,7 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
   if (rc != SK_OK) return rc;
   rc = resolve_cfg(fam, &d, sms, c);
   if (rc != SK_OK) return rc;
+  if (c->BN == 512 && !single) return fail_msg(SK_ERR_UNSUPPORTED, "256 x 512 tiles: single-problem calls only");
   for (const Norm &n : *work) {
     if (fam != FAM_F32 || c->tc32) {
       rc = check_tc_alignment(n);
@@ -1215,15 +1249,22 @@ sk_status prepare(const sk_problem *problems, int count, const sk_config *cfg, i
 // (cached per device and variant).
 int pair_clusters(int dev, const Cfg &c, bool f32out, bool grouped) {
   static std::mutex mu;
-  static int cache[64][3][2][2][2][16] = {};
+  static int cache[64][3][3][2][2][16] = {};
   const int fi = c.fam == FAM_E4M3 ? 1 : c.fam == FAM_F32 ? 2 : 0;
-  const int bi = c.BN == 128 ? 1 : 0;
+  const int bi = c.BN == 128 ? 1 : c.BN == 512 ? 2 : 0;
   const int st = c.stages & 15;
   std::lock_guard<std::mutex> lk(mu);
   int &slot = cache[dev][fi][bi][f32out][grouped][st];
   if (slot == 0) {
     int n = 0;
-    if (c.fam == FAM_BF16 && c.BN == 128) {
+    if (c.BN == 512) {   // single-problem BF16 / E4M3 pairs
+      if (!grouped && c.fam == FAM_BF16)
+        n = f32out ? pair_max_clusters<IN_BF16, float, 512, 1>(c.stages)
+                   : pair_max_clusters<IN_BF16, __nv_bfloat16, 512, 1>(c.stages);
+      else if (!grouped && c.fam == FAM_E4M3)
+        n = f32out ? pair_max_clusters<IN_E4M3, float, 512, 1>(c.stages)
+                   : pair_max_clusters<IN_E4M3, __nv_bfloat16, 512, 1>(c.stages);
+    } else if (c.fam == FAM_BF16 && c.BN == 128) {
       if (grouped)
         n = f32out ? pair_max_clusters<IN_BF16, float, 128, MAXP_GROUPED>(c.stages)
                    : pair_max_clusters<IN_BF16, __nv_bfloat16, 128, MAXP_GROUPED>(c.stages);

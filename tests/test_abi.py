@@ -104,12 +104,13 @@ def test_workspace_size(sk):
     q8 = sk.shape_problem(384, 384, 2048, dtype="e4m3")
     c = sk.api._cfg({"num_ctas": 148, "tile_m": 256, "tile_n": 128})
     assert B.sk_workspace_size(ctypes.byref(q8), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_ERR_UNSUPPORTED
-    # whatever the library picks fits the default workspace (every SM, 128 x 256 slots)
+    # whatever the library picks fits one 128 x 512 slot per CTA (the widest
+    # tile, 256 x 512 pairs, which it picks for 8192^3)
     for shape in [(384, 384, 2048), (8192, 8192, 8192), (128, 8192, 16384)]:
         c = sk.api._cfg({"num_ctas": 148})
         q = sk.shape_problem(*shape)
         assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-        assert n.value <= 256 + 4096 + 148 * 128 * 256 * 4
+        assert n.value <= 256 + 4096 + 148 * 128 * 512 * 4
     # the last-arriver fixup keeps a second slot per CTA (owner segments)
     for tile in ((128, 128), (128, 256), (256, 256)):
         c = sk.api._cfg({"num_ctas": 148, "tile_m": tile[0], "tile_n": tile[1], "fixup": "last_arriver"})
@@ -157,14 +158,15 @@ def test_default_workspace_fits_both_fixups(sk):
     B = sk.binding
     n = ctypes.c_size_t(0)
     sms = 148
-    default = 256 + 4096 + 2 * sms * 128 * 256 * 4
+    default = 256 + 4096 + 2 * sms * 128 * 512 * 4
     assert sk.api.default_workspace_bytes(sms) == default
     for fix in ("owner", "last_arriver"):
         for shape in [(384, 384, 2048), (8192, 8192, 8192), (128, 8192, 16384), (1536, 1536, 8192)]:
-            c = sk.api._cfg({"num_ctas": sms, "fixup": fix})
-            q = sk.shape_problem(*shape)
-            assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
-            assert n.value <= default
+            for tiles in ({}, {"tile_m": 256, "tile_n": 512}):   # library choice; the widest tile
+                c = sk.api._cfg({"num_ctas": sms, "fixup": fix, **tiles})
+                q = sk.shape_problem(*shape)
+                assert B.sk_workspace_size(ctypes.byref(q), 1, ctypes.byref(c), ctypes.byref(n)) == B.SK_OK
+                assert n.value <= default
 
 
 def test_gemm_without_device_reports_no_device(sk):
@@ -527,3 +529,27 @@ def test_cluster_split_eligibility(sk):
                                 ((1536, 1536, 8192), {"tile_m": 256, "num_ctas": 144}, "bf16", 2)]:
         rc, _ = q(shape, {**xs, **cfg}, dtype=dt, count=cnt)
         assert rc == B.SK_ERR_UNSUPPORTED, (shape, cfg, dt, cnt)
+
+
+def test_wide_pair_tile_plans(sk):
+    """256 x 512 pair tiles: the tile grid is ceil(M/256) x ceil(N/512), the
+    workspace holds a 128 x 512 FP32 slot per CTA, and the tile is refused
+    off a CTA pair, for FP32, and for groups."""
+    B = sk.binding
+    p = sk.shape_problem(8192, 8192, 8192)
+    info = sk.plan(p, sk.Config(tile_m=256, tile_n=512, mode="dp"), num_sms=152)
+    assert (info.tile_m, info.tile_n, info.num_ctas, info.tiles) == (256, 512, 76, 32 * 16)
+    assert info.stages == 4   # 48 KB stages
+    assert info.workspace_bytes >= 152 * 128 * 512 * 4
+    r = sk.plan(sk.shape_problem(700, 1300, 1000), sk.Config(tile_m=256, tile_n=512), num_sms=152)
+    assert r.tiles == 3 * 3
+    fp8 = sk.plan(sk.shape_problem(4096, 4096, 4096, dtype="e4m3"), sk.Config(tile_m=256, tile_n=512), num_sms=152)
+    assert fp8.tile_n == 512
+    for bad in (dict(tile_m=128, tile_n=512), dict(tile_m=256, tile_n=384)):
+        with pytest.raises(sk.SkError):
+            sk.plan(p, sk.Config(**bad), num_sms=152)
+    with pytest.raises(sk.SkError):
+        sk.plan(sk.shape_problem(1024, 1024, 1024, dtype="f32"), sk.Config(tile_m=256, tile_n=512), num_sms=152)
+    with pytest.raises(sk.SkError):
+        sk.plan([p, p], sk.Config(tile_m=256, tile_n=512), num_sms=152)
+    assert B.SK_OK == 0

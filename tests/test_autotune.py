@@ -23,7 +23,7 @@ def test_candidates_ranked_and_valid(sk):
     preds = [u for _, u in c]
     assert preds == sorted(preds) and preds[0] > 0
     tiles = {(cfg.tile_m, cfg.tile_n) for cfg, _ in c}
-    assert tiles == {(128, 128), (128, 256), (256, 256)}
+    assert tiles == {(128, 128), (128, 256), (256, 256), (256, 512)}
     # transposed A: the CTA pair reads MN-major operands too
     p = sk.shape_problem(4096, 4096, 4096, a_layout="col")
     assert {cfg.tile_m for cfg, _ in sk.autotune.candidates(p, num_sms=152)} == {128, 256}

@@ -46,7 +46,7 @@ def test_bf16_pair_first_small_dp(m):
     assert np.array_equal(to_np(c), ref)
 
 
-TILES = [(128, 128), (128, 256), (256, 128), (256, 256)]
+TILES = [(128, 128), (128, 256), (256, 128), (256, 256), (256, 512)]
 
 
 @pytest.mark.parametrize("tile", TILES)

@@ -109,7 +109,7 @@ def _check(m, shapes, cfg, grouped=False, out_dtype=torch.bfloat16):
 
 @pytest.mark.parametrize("mode", ["dp", "sk", "hybrid1", "hybrid2"])
 @pytest.mark.parametrize("ctas", [1, 7, 76, 151, 152])
-@pytest.mark.parametrize("tile", [(128, 128), (128, 256), (256, 256)])
+@pytest.mark.parametrize("tile", [(128, 128), (128, 256), (256, 256), (256, 512)])
 def test_coverage_single(m, mode, ctas, tile):
     if tile[0] == 256 and ctas < 2:
         ctas = 2   # a pair is the smallest unit

@@ -130,3 +130,40 @@ def test_default_workspace_per_stream(m):
     for s, ws, c in zip((s1, s2), wss, outs):
         assert ws.status() == 0
         assert np.array_equal(to_np(c), ref)
+
+
+LONG_K = 1048616   # 16385 k-blocks of 64, the last one ragged (40)
+_long_k_cache = {}
+
+
+def _long_k_case(n):
+    """Integer operands n x LONG_K and LONG_K x n and their FP64 oracle
+    product, computed once per n."""
+    if n not in _long_k_cache:
+        a, b = workloads.gemm_inputs(n, n, LONG_K, dtype="bf16", seed=131, dist="int")
+        _long_k_cache[n] = (a, b, oracle.gemm(a, b)[0])
+    return _long_k_cache[n]
+
+
+@pytest.mark.parametrize("tile,mode,fixup,ctas", [
+    ((128, 128), "sk", "owner", 0),           # 152 units on one tile: the owner adds 151 partials
+    ((128, 128), "sk", "last_arriver", 0),
+    ((128, 128), "sk", "split", 145),         # 145 equal ranges of 113 k-blocks
+    ((128, 128), "dp", "owner", 0),           # one unit walks all 16385 k-blocks
+    ((256, 256), "sk", "owner", 0),           # 76 CTA pairs on one tile
+    ((256, 256), "dp", "owner", 0),
+])
+def test_bf16_long_k_single_tile_exact(m, tile, mode, fixup, ctas):
+    """K ~ 2^20 on a single output tile: every unit of the grid holds a range
+    of the same tile (the longest fixup chain the unit count allows), or one
+    unit runs the whole k-loop.  Integer inputs in [-2, 2] keep every partial
+    and the sum below 2^24, so the FP32 result equals the FP64 oracle."""
+    M, N = tile
+    a, b, ref = _long_k_case(M)
+    d = dev()
+    cfg = m.Config(mode=mode, tile_m=tile[0], tile_n=tile[1], fixup=fixup, num_ctas=ctas, min_iters_per_unit=1)
+    c = m.gemm(same_strides(a, d), same_strides(b, d), out_dtype=torch.float32, config=cfg)
+    assert m.default_workspace(d).status() == 0
+    info = m.plan(m.make_problem(a, b, torch.empty(M, N, dtype=torch.float32)), cfg, num_sms=152)
+    assert info.tiles == 1
+    assert np.array_equal(to_np(c), ref), (tile, mode, fixup)
