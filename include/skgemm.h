@@ -326,13 +326,24 @@ SK_API sk_status sk_gemm_grouped(const sk_problem *problems, int count,
  * leading dimension lddc, type fwd->c_type), compute
  *     dA = dC * B^T   (m x k, same type/layout as A, leading dimension ldda)
  *     dB = A^T * dC   (k x n, same type/layout as B, leading dimension lddb)
- * in one grouped launch of two Stream-K GEMMs whose operands are read in
- * transposed order directly (no transposed copies).  Either of dA, dB may
- * be NULL to skip it.  BF16 only. */
+ * in one grouped launch of two Stream-K GEMMs.  Either of dA, dB may be
+ * NULL to skip it.  BF16 only.  An operand these GEMMs would read MN-major
+ * (a forward K-major operand, and dC for dB) is first copied to K-major
+ * layout in the workspace, past the GEMMs' own bytes, when ws_bytes holds
+ * sk_gemm_backward_workspace_size(); with a smaller workspace (at least
+ * sk_workspace_size of the two GEMMs) they read the operands in place,
+ * about 1.4x slower.  The result is the same either way: a copy changes no
+ * value and the GEMMs' summation order does not depend on the layout. */
 SK_API sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc,
                            void *dA, int64_t ldda, void *dB, int64_t lddb,
                            const sk_config *cfg, void *ws, size_t ws_bytes,
                            sk_stream_t stream);
+
+/* Workspace bytes with which sk_gemm_backward (same fwd shape/layouts,
+ * need_dA / need_dB = whether dA / dB is computed, same config) reads
+ * K-major copies of its MN-major operands.  Pointers in fwd are ignored. */
+SK_API sk_status sk_gemm_backward_workspace_size(const sk_problem *fwd, int need_dA, int need_dB,
+                                                 const sk_config *cfg, size_t *bytes);
 
 /* Per-tensor FP8 quantisation: scale = amax(|x|)/448 (1 if x == 0),
  * q = E4M3(x / scale) rounded to nearest even and saturated to +-448.

@@ -249,8 +249,16 @@ def gemm_backward(A: torch.Tensor, Bm: torch.Tensor, dC: torch.Tensor, *, need_d
     fwd.alpha, fwd.beta = 1.0, 0.0
     ldda = layout_of(dA, B.SK_ROW_MAJOR)[1] if dA is not None else 0
     lddb = layout_of(dB, B.SK_COL_MAJOR)[1] if dB is not None else 0
-    ws = workspace or default_workspace(A.device)
     cfg = _cfg(config)
+    if workspace is None:
+        # room for K-major copies of the operands the backward GEMMs would
+        # read MN-major (the library transposes them there first)
+        need = ctypes.c_size_t(0)
+        B.check(B.sk_gemm_backward_workspace_size(ctypes.byref(fwd), int(need_dA), int(need_dB), ctypes.byref(cfg),
+                                                  ctypes.byref(need)), "sk_gemm_backward_workspace_size")
+        ws = default_workspace(A.device, need.value)
+    else:
+        ws = workspace
     B.check(B.sk_gemm_backward(ctypes.byref(fwd), _ptr(dC), lddc, _ptr(dA), ldda, _ptr(dB), lddb,
                                ctypes.byref(cfg), ws.ptr, ws.nbytes, _stream()), "sk_gemm_backward")
     return dA, dB

@@ -3,6 +3,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -61,6 +62,61 @@ __global__ void quant_kernel(const float *x, int64_t n, uint8_t *q, float *scale
   }
 }
 
+// dst = transpose of src for 16-bit elements: src is rows x cols row-major
+// (leading dimension ld_src), dst cols x rows row-major (ld_dst).  64 x 64
+// tiles through shared memory (row pitch 66 elements: a column gather hits
+// each bank at most twice), 16-byte global loads and stores where a group of
+// 8 elements lies inside the matrix and both row pitches are multiples of 8
+// elements (the caller's 16-byte-aligned operands), element by element at the
+// ragged edges.  A grid-stride loop over tiles keeps any size in one launch.
+__global__ void __launch_bounds__(256) transpose16_kernel(const uint16_t *__restrict__ src, int64_t rows, int64_t cols,
+                                                          int64_t ld_src, uint16_t *__restrict__ dst, int64_t ld_dst,
+                                                          int vec) {
+  __shared__ __align__(16) uint16_t tile[64][66];
+  const int64_t tr = (rows + 63) / 64, tc = (cols + 63) / 64;
+  const int t = threadIdx.x;
+  for (int64_t tile_id = blockIdx.x; tile_id < tr * tc; tile_id += gridDim.x) {
+    const int64_t r0 = (tile_id / tc) * 64, c0 = (tile_id % tc) * 64;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int r = t / 8 + 32 * p, c = 8 * (t % 8);
+      uint16_t v[8];
+      const int64_t gr = r0 + r, gc = c0 + c;
+      if (vec && gr < rows && gc + 8 <= cols) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(src + gr * ld_src + gc);
+        std::memcpy(v, &q, 16);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = (gr < rows && gc + e < cols) ? src[gr * ld_src + gc + e] : (uint16_t)0;
+      }
+#pragma unroll
+      for (int e = 0; e < 8; e += 2)
+        *reinterpret_cast<uint32_t *>(&tile[r][c + e]) = (uint32_t)v[e] | ((uint32_t)v[e + 1] << 16);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int j = t / 8 + 32 * p, i = 8 * (t % 8);   // dst row j (src column), dst columns i .. i+7
+      const int64_t gr = c0 + j, gc = r0 + i;
+      if (gr < cols) {
+        uint16_t v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = tile[i + e][j];
+        if (vec && gc + 8 <= rows) {
+          uint4 q;
+          std::memcpy(&q, v, 16);
+          *reinterpret_cast<uint4 *>(dst + gr * ld_dst + gc) = q;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            if (gc + e < rows) dst[gr * ld_dst + gc + e] = v[e];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 struct UploadBlock {
   uint4 *dst;
   uint32_t n16;   // 16-byte words carried
@@ -75,6 +131,18 @@ __global__ void upload_kernel(const __grid_constant__ UploadBlock b) {
 }
 
 }  // namespace
+
+cudaError_t launch_transpose16(const void *src, int64_t rows, int64_t cols, int64_t ld_src, void *dst, int64_t ld_dst,
+                               int sms, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  const int vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15u) == 0 &&
+                  ld_src % 8 == 0 && ld_dst % 8 == 0;
+  const int64_t tiles = ((rows + 63) / 64) * ((cols + 63) / 64);
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)std::max(1, sms) * 8);
+  transpose16_kernel<<<grid, 256, 0, st>>>(static_cast<const uint16_t *>(src), rows, cols, ld_src,
+                                           static_cast<uint16_t *>(dst), ld_dst, vec);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_upload(void *dst, const void *src, size_t bytes, cudaStream_t st) {
   if ((bytes & 15u) || (reinterpret_cast<uintptr_t>(dst) & 15u)) return cudaErrorInvalidValue;

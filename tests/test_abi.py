@@ -553,3 +553,26 @@ def test_wide_pair_tile_plans(sk):
     with pytest.raises(sk.SkError):
         sk.plan([p, p], sk.Config(tile_m=256, tile_n=512), num_sms=152)
     assert B.SK_OK == 0
+
+
+def test_backward_workspace_size(sk):
+    """The backward's workspace: the two GEMMs' bytes, then one K-major copy
+    per operand they would read MN-major (for the usual row-major A and
+    column-major B: B for dA, A and dC for dB)."""
+    B = sk.binding
+    M, N, K = 8192, 11008, 4096
+    fwd = sk.shape_problem(M, N, K)
+    cfg = sk.Config(num_ctas=152).to_c()   # an SM count: no device needed
+    n = ctypes.c_size_t(0)
+    assert B.sk_gemm_backward_workspace_size(ctypes.byref(fwd), 1, 1, ctypes.byref(cfg), ctypes.byref(n)) == B.SK_OK
+    copies = (K * N + K * M + M * N) * 2
+    assert copies <= n.value <= copies + 256 + 4096 + 2 * 152 * 128 * 512 * 4 + 4 * 256
+    # dA only: B's copy
+    assert B.sk_gemm_backward_workspace_size(ctypes.byref(fwd), 1, 0, ctypes.byref(cfg), ctypes.byref(n)) == B.SK_OK
+    assert K * N * 2 <= n.value < (K * N + K * M) * 2
+    # both operands already in the backward's K-major order: no copies
+    t = sk.shape_problem(M, N, K, a_layout="col", b_layout="row")
+    assert B.sk_gemm_backward_workspace_size(ctypes.byref(t), 1, 0, ctypes.byref(cfg), ctypes.byref(n)) == B.SK_OK
+    assert n.value < 256 + 4096 + 2 * 152 * 128 * 512 * 4 + 256
+    f32 = sk.shape_problem(64, 64, 64, dtype="f32")
+    assert B.sk_gemm_backward_workspace_size(ctypes.byref(f32), 1, 1, ctypes.byref(cfg), ctypes.byref(n)) == B.SK_ERR_UNSUPPORTED

@@ -230,3 +230,43 @@ def test_grouped_many_problems_fp32(m, f32k):
     assert m.default_workspace(d).status() == 0
     for i, (o, r) in enumerate(zip(outs, refs)):
         assert np.array_equal(to_np(o), r), (f32k, i, shapes[i])
+
+
+def _backward_ws(m, a, b, d, copies):
+    """A workspace with (copies=True) or without room for the K-major copies
+    sk_gemm_backward makes of MN-major operands: the copies end the size the
+    library asks for, so 256 bytes less holds the GEMMs' own bytes but not
+    the copies."""
+    import ctypes
+    B = m.binding
+    fwd = m.make_problem(a, b, torch.empty(a.shape[0], b.shape[1], dtype=torch.bfloat16, device=d))
+    cfg = m.Config().to_c()
+    n = ctypes.c_size_t(0)
+    B.check(B.sk_gemm_backward_workspace_size(ctypes.byref(fwd), 1, 1, ctypes.byref(cfg), ctypes.byref(n)))
+    return m.Workspace(d, n.value if copies else n.value - 256)
+
+
+@pytest.mark.parametrize("al,bl", [("row", "col"), ("row", "row"), ("col", "col"), ("col", "row")])
+def test_backward_copies_equal_in_place(m, al, bl):
+    """The backward GEMMs on K-major copies of their MN-major operands (made
+    by the library's transpose kernel in the workspace) give the same bits
+    as the GEMMs reading the operands in place; ragged extents (M = 300 with
+    a padded leading dimension) take the transpose's element-by-element
+    edge path."""
+    M, N, K = 300, 392, 1000
+    d = dev()
+    a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=58)
+    g = workloads.normal((M, N), seed=59).to(torch.bfloat16).to(d)
+    # A col-major: storage K x M with a leading dimension padded to 304
+    A = (torch.empty_strided((M, K), (1, 304), dtype=torch.bfloat16, device=d).copy_(a) if al == "col"
+         else a.to(d))
+    Bm = (torch.empty_strided((K, N), (1, K), dtype=torch.bfloat16, device=d).copy_(b) if bl == "col"
+          else b.contiguous().to(d))
+    w_copy, w_plain = _backward_ws(m, A, Bm, d, True), _backward_ws(m, A, Bm, d, False)
+    assert w_copy.nbytes > w_plain.nbytes
+    dA1, dB1 = m.gemm_backward(A, Bm, g, workspace=w_copy)
+    dA2, dB2 = m.gemm_backward(A, Bm, g, workspace=w_plain)
+    assert w_copy.status() == 0 and w_plain.status() == 0
+    assert torch.equal(dA1, dA2) and torch.equal(dB1, dB2)
+    assert_within_bound(dA1, g.cpu(), b.t(), out="bf16", what="dA (copies)")
+    assert_within_bound(dB1, a.t(), g.cpu(), out="bf16", what="dB (copies)")
