@@ -345,6 +345,15 @@ SK_API sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t
 SK_API sk_status sk_gemm_backward_workspace_size(const sk_problem *fwd, int need_dA, int need_dB,
                                                  const sk_config *cfg, size_t *bytes);
 
+/* dst = transpose of src for 16-bit elements (BF16): src is rows x cols
+ * row-major with leading dimension ld_src >= cols, dst cols x rows row-major
+ * with ld_dst >= rows; device pointers, 2-byte aligned (16-byte aligned
+ * pointers and leading dimensions that are multiples of 8 take the vector
+ * path).  The kernel sk_gemm_backward uses for its K-major operand copies;
+ * asynchronous on `stream`.  rows or cols == 0: nothing to do. */
+SK_API sk_status sk_transpose16(const void *src, int64_t rows, int64_t cols, int64_t ld_src,
+                                void *dst, int64_t ld_dst, sk_stream_t stream);
+
 /* Per-tensor FP8 quantisation: scale = amax(|x|)/448 (1 if x == 0),
  * q = E4M3(x / scale) rounded to nearest even and saturated to +-448.
  * x: n float32 values; q: n bytes; scale_out: one float; amax_work: one

@@ -12,11 +12,11 @@ _load()
 
 from .api import (Config, Workspace, default_workspace, gemm, gemm_backward,  # noqa: E402
                   grouped_gemm, layout_of, make_problem, plan, quantize_e4m3,
-                  shape_problem, trace_gemm, unit_items)
+                  shape_problem, trace_gemm, transpose16, unit_items)
 from .autograd import SkMatmul, sk_matmul  # noqa: E402
 from . import autotune  # noqa: E402
 from .pipeline import HostGemmPipeline  # noqa: E402
 
 __all__ = ["binding", "SkError", "Config", "Workspace", "default_workspace", "gemm", "HostGemmPipeline",
            "gemm_backward", "grouped_gemm", "layout_of", "make_problem", "plan",
-           "quantize_e4m3", "shape_problem", "trace_gemm", "unit_items", "SkMatmul", "sk_matmul", "autotune"]
+           "quantize_e4m3", "shape_problem", "trace_gemm", "transpose16", "unit_items", "SkMatmul", "sk_matmul", "autotune"]

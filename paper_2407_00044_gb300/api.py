@@ -264,6 +264,21 @@ def gemm_backward(A: torch.Tensor, Bm: torch.Tensor, dC: torch.Tensor, *, need_d
     return dA, dB
 
 
+def transpose16(x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    """x.T materialised row-major by the library's transpose kernel (16-bit
+    element types; x row-major with unit column stride)."""
+    if x.dim() != 2 or x.element_size() != 2 or x.stride(1) != 1:
+        raise ValueError("expected a row-major 2-D tensor of a 16-bit type")
+    rows, cols = x.shape
+    if out is None:
+        out = torch.empty((cols, rows), dtype=x.dtype, device=x.device)
+    if out.shape != (cols, rows) or out.stride(1) != 1 or out.dtype != x.dtype:
+        raise ValueError("out must be a row-major (cols x rows) tensor of x's type")
+    B.check(B.sk_transpose16(_ptr(x), rows, cols, max(1, x.stride(0)), _ptr(out), max(1, out.stride(0)), _stream()),
+            "sk_transpose16")
+    return out
+
+
 def quantize_e4m3(x: torch.Tensor):
     """Per-tensor FP8 quantisation on the GPU: returns (codes uint8, scale)."""
     x = x.contiguous()

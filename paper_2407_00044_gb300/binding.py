@@ -104,6 +104,7 @@ _SIGNATURES = {
                                ctypes.c_int64, _P(sk_config), _vp, ctypes.c_size_t, _vp]),
     "sk_gemm_backward_workspace_size": (_st, [_P(sk_problem), ctypes.c_int, ctypes.c_int, _P(sk_config),
                                               _P(ctypes.c_size_t)]),
+    "sk_transpose16": (_st, [_vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _vp, ctypes.c_int64, _vp]),
     "sk_quantize_e4m3": (_st, [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]),
     "sk_get_status": (_st, [_vp, ctypes.c_size_t, _vp, ctypes.c_int, _P(ctypes.c_int)]),
     "sk_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -166,6 +167,10 @@ def sk_gemm_backward(fwd, dC, lddc, dA, ldda, dB, lddb, cfg, ws, ws_bytes, strea
 
 def sk_gemm_backward_workspace_size(fwd, need_dA, need_dB, cfg, bytes_out):
     return load().sk_gemm_backward_workspace_size(fwd, need_dA, need_dB, cfg, bytes_out)
+
+
+def sk_transpose16(src, rows, cols, ld_src, dst, ld_dst, stream):
+    return load().sk_transpose16(src, rows, cols, ld_src, dst, ld_dst, stream)
 
 
 def sk_quantize_e4m3(x, n, q, scale_out, amax_work, stream):

@@ -68,48 +68,60 @@ __global__ void quant_kernel(const float *x, int64_t n, uint8_t *q, float *scale
 // each bank at most twice), 16-byte global loads and stores where a group of
 // 8 elements lies inside the matrix and both row pitches are multiples of 8
 // elements (the caller's 16-byte-aligned operands), element by element at the
-// ragged edges.  A grid-stride loop over tiles keeps any size in one launch.
+// ragged edges.  A grid-stride loop over tiles keeps any size in one launch;
+// each thread loads its part of the next tile into registers before it
+// gathers and stores the current one, so a tile's load latency overlaps the
+// previous tile's stores.
 __global__ void __launch_bounds__(256) transpose16_kernel(const uint16_t *__restrict__ src, int64_t rows, int64_t cols,
                                                           int64_t ld_src, uint16_t *__restrict__ dst, int64_t ld_dst,
                                                           int vec) {
   __shared__ __align__(16) uint16_t tile[64][66];
-  const int64_t tr = (rows + 63) / 64, tc = (cols + 63) / 64;
+  const int64_t tr = (rows + 63) / 64, tc = (cols + 63) / 64, ntiles = tr * tc;
   const int t = threadIdx.x;
-  for (int64_t tile_id = blockIdx.x; tile_id < tr * tc; tile_id += gridDim.x) {
+  uint16_t v[2][8];
+  auto load = [&](int64_t tile_id) {
+    const int64_t r0 = (tile_id / tc) * 64, c0 = (tile_id % tc) * 64;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int64_t gr = r0 + t / 8 + 32 * p, gc = c0 + 8 * (t % 8);
+      if (vec && gr < rows && gc + 8 <= cols) {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(src + gr * ld_src + gc));
+        std::memcpy(v[p], &q, 16);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[p][e] = (gr < rows && gc + e < cols) ? src[gr * ld_src + gc + e] : (uint16_t)0;
+      }
+    }
+  };
+  int64_t tile_id = blockIdx.x;
+  if (tile_id < ntiles) load(tile_id);
+  for (; tile_id < ntiles; tile_id += gridDim.x) {
     const int64_t r0 = (tile_id / tc) * 64, c0 = (tile_id % tc) * 64;
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int r = t / 8 + 32 * p, c = 8 * (t % 8);
-      uint16_t v[8];
-      const int64_t gr = r0 + r, gc = c0 + c;
-      if (vec && gr < rows && gc + 8 <= cols) {
-        const uint4 q = *reinterpret_cast<const uint4 *>(src + gr * ld_src + gc);
-        std::memcpy(v, &q, 16);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = (gr < rows && gc + e < cols) ? src[gr * ld_src + gc + e] : (uint16_t)0;
-      }
 #pragma unroll
       for (int e = 0; e < 8; e += 2)
-        *reinterpret_cast<uint32_t *>(&tile[r][c + e]) = (uint32_t)v[e] | ((uint32_t)v[e + 1] << 16);
+        *reinterpret_cast<uint32_t *>(&tile[r][c + e]) = (uint32_t)v[p][e] | ((uint32_t)v[p][e + 1] << 16);
     }
     __syncthreads();
+    if (tile_id + gridDim.x < ntiles) load(tile_id + gridDim.x);   // in flight during the stores below
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
       const int j = t / 8 + 32 * p, i = 8 * (t % 8);   // dst row j (src column), dst columns i .. i+7
       const int64_t gr = c0 + j, gc = r0 + i;
       if (gr < cols) {
-        uint16_t v[8];
+        uint16_t w[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = tile[i + e][j];
+        for (int e = 0; e < 8; ++e) w[e] = tile[i + e][j];
         if (vec && gc + 8 <= rows) {
           uint4 q;
-          std::memcpy(&q, v, 16);
-          *reinterpret_cast<uint4 *>(dst + gr * ld_dst + gc) = q;
+          std::memcpy(&q, w, 16);
+          __stcs(reinterpret_cast<uint4 *>(dst + gr * ld_dst + gc), q);
         } else {
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            if (gc + e < rows) dst[gr * ld_dst + gc + e] = v[e];
+            if (gc + e < rows) dst[gr * ld_dst + gc + e] = w[e];
         }
       }
     }

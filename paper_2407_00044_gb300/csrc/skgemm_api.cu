@@ -591,10 +591,17 @@ double plan_dram_bytes(const std::vector<Norm> &work, const PlanOut &pl, const C
 // memory, as a fraction of a full spill to the workspace (estimate).
 constexpr double kXsExchangeFrac = 0.35;
 
+constexpr double kGroupedIterFactor = 1.07;
+
 double predict_ns(const std::vector<Norm> &work, const PlanOut &pl, const Cfg &c) {
-  const ModelCoeffs k = model_coeffs(c);
+  ModelCoeffs k = model_coeffs(c);
   const Sched &s = pl.s;
   if (s.num_problems <= 0) return k.launch_ns;
+  // The grouped kernel (problem table, per-item tensor-map selection) runs a
+  // k-block about 7 % slower than the single-problem one: the two backward
+  // GEMMs of 8192 x 11008 x 4096 took 842 us as one grouped launch and
+  // 784 us as two single launches on the same tiles.
+  if (work.size() > 1) k.iter_ns *= kGroupedIterFactor;
   std::vector<std::vector<Item>> items((size_t)c.g);
   double longest_mac = 0;
   for (int u = 0; u < c.g; ++u) {
@@ -1584,7 +1591,32 @@ sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc, 
       }
     }
   }
+  // One grouped launch (Stream-K across both problems) or two single-problem
+  // launches (the single-problem kernels, wider tiles), whichever the
+  // runtime model predicts faster; both write the same results' values up to
+  // the summation order of each plan.
+  if (n == 2) {
+    sk_plan_info g, s0, s1;
+    if (sk_plan_query(pr, 2, cfg, 0, &g) == SK_OK && sk_plan_query(&pr[0], 1, cfg, 0, &s0) == SK_OK &&
+        sk_plan_query(&pr[1], 1, cfg, 0, &s1) == SK_OK && s0.predicted_us + s1.predicted_us < g.predicted_us) {
+      sk_status rc = run(&pr[0], 1, cfg, ws, ws_bytes, st, 1);
+      if (rc != SK_OK) return rc;
+      return run(&pr[1], 1, cfg, ws, ws_bytes, st, 1);
+    }
+  }
   return run(pr, n, cfg, ws, ws_bytes, st, MAX_PROBLEMS);
+}
+
+sk_status sk_transpose16(const void *src, int64_t rows, int64_t cols, int64_t ld_src, void *dst, int64_t ld_dst,
+                         sk_stream_t stream) {
+  if (rows < 0 || cols < 0 || ((rows > 0 && cols > 0) && (!src || !dst))) return SK_ERR_INVALID_ARG;
+  if (ld_src < cols || ld_dst < rows) return SK_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(src) & 1u) || (reinterpret_cast<uintptr_t>(dst) & 1u)) return SK_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail_msg(SK_ERR_NO_DEVICE, "no CUDA device");
+  return cuda_err(launch_transpose16(src, rows, cols, ld_src, dst, ld_dst, sms, reinterpret_cast<cudaStream_t>(stream)),
+                  "transpose launch");
 }
 
 sk_status sk_quantize_e4m3(const float *x, int64_t n, uint8_t *q, float *scale_out, float *amax_work,

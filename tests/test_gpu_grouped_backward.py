@@ -270,3 +270,17 @@ def test_backward_copies_equal_in_place(m, al, bl):
     assert torch.equal(dA1, dA2) and torch.equal(dB1, dB2)
     assert_within_bound(dA1, g.cpu(), b.t(), out="bf16", what="dA (copies)")
     assert_within_bound(dB1, a.t(), g.cpu(), out="bf16", what="dB (copies)")
+
+
+@pytest.mark.parametrize("shape,ld_pad", [((64, 64), 0), ((4096, 11008), 0), ((300, 1000), 8), ((1, 8), 0),
+                                          ((7, 13), 3), ((130, 72), 0), ((8192, 8), 0)])
+def test_transpose16_equals_torch(m, shape, ld_pad):
+    """The backward's transpose kernel: bit-exact against torch's transpose,
+    aligned (16-byte vector path) and ragged or odd-pitch (element path)."""
+    d = dev()
+    R, C = shape
+    base = torch.arange(R * (C + ld_pad), device=d, dtype=torch.int32).to(torch.int16).view(torch.bfloat16)
+    x = base.view(R, C + ld_pad)[:, :C]
+    y = m.transpose16(x)
+    torch.cuda.synchronize()
+    assert torch.equal(y.view(torch.int16), x.t().contiguous().view(torch.int16))
