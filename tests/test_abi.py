@@ -576,3 +576,23 @@ def test_backward_workspace_size(sk):
     assert n.value < 256 + 4096 + 2 * 152 * 128 * 512 * 4 + 256
     f32 = sk.shape_problem(64, 64, 64, dtype="f32")
     assert B.sk_gemm_backward_workspace_size(ctypes.byref(f32), 1, 1, ctypes.byref(cfg), ctypes.byref(n)) == B.SK_ERR_UNSUPPORTED
+
+
+def test_model_picks_wide_tile_for_long_k_dp(sk):
+    """The runtime model takes 256 x 512 pairs, data-parallel, where they
+    measured faster (long K, few tiles per pair) and 256 x 256 pairs where
+    they measured slower (K = 4096, many tiles per pair, short shapes)."""
+    def pick(M, N, K):
+        i = sk.plan(sk.shape_problem(M, N, K), None, num_sms=152)
+        return (i.tile_m, i.tile_n, i.mode)
+    DP = sk.binding.SK_MODE_DP
+    for shape in [(8192, 8192, 8192), (8192, 8192, 16384), (6144, 6144, 12288)]:
+        assert pick(*shape) == (256, 512, DP), shape
+    for shape in [(8192, 8192, 4096), (4096, 14336, 4096), (16384, 16384, 4096), (3840, 4096, 4096),
+                  (2048, 7168, 1024), (1536, 1536, 8192)]:
+        assert pick(*shape)[1] != 512, shape
+    # never for groups, FP32, or Stream-K / hybrid plans of the library's own
+    g = sk.plan([sk.shape_problem(8192, 8192, 8192)] * 2, None, num_sms=152)
+    assert g.tile_n != 512
+    f = sk.plan(sk.shape_problem(8192, 8192, 8192, dtype="f32"), None, num_sms=152)
+    assert f.tile_n != 512

@@ -147,3 +147,16 @@ def test_wide_rejections(m):
     g = torch.zeros(512, 64, dtype=torch.float32, device=d).t()
     with pytest.raises(m.SkError):
         m.gemm(f, g, config=m.Config(tile_m=256, tile_n=512))
+
+
+def test_library_picks_wide_tile_at_8192_cube(m):
+    """8192^3: the library's own choice is the 256 x 512 DP tile, and it
+    equals the explicit configuration bit for bit."""
+    d = dev()
+    A = workloads.device_uniform((8192, 8192), seed=19, device=d)
+    B = workloads.device_uniform((8192, 8192), seed=20, device=d).t()
+    c = m.gemm(A, B)
+    info = m.plan(m.make_problem(A, B, c))
+    assert (info.tile_m, info.tile_n, info.mode) == (256, 512, m.binding.SK_MODE_DP)
+    assert torch.equal(c, m.gemm(A, B, config=m.Config(mode="dp", **W)))
+    assert m.default_workspace(d).status() == 0
