@@ -164,15 +164,15 @@ def test_library_picks_wide_tile_at_8192_cube(m):
 
 @pytest.mark.parametrize("beta", [0.0, 0.5])
 def test_wide_f32_out_plain_stores(m, beta):
-    """FP32 C whose row pitch TMA cannot store (ldc = N + 2 floats) or with
+    """FP32 C whose row pitch TMA cannot store (ldc = N + 1 floats) or with
     beta != 0: the per-thread store path of the 256 x 512 tile, ragged N."""
     M, N, K = 520, 1030, 2048
     a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=21)
     A, B = _dev(a, b)
     d = dev()
-    C = torch.empty_strided((M, N), (N + 2, 1), dtype=torch.float32, device=d)
+    C = torch.empty_strided((M, N), (N + 1, 1), dtype=torch.float32, device=d)
     c0 = workloads.uniform((M, N), seed=22)
-    C_in = (torch.empty_strided((M, N), (N + 2, 1), dtype=torch.float32, device=d).copy_(c0)
+    C_in = (torch.empty_strided((M, N), (N + 1, 1), dtype=torch.float32, device=d).copy_(c0)
             if beta != 0.0 else None)   # C_in shares C's strides
     m.gemm(A, B, C, beta=beta, C_in=C_in, config=m.Config(mode="hybrid2", **W))
     assert m.default_workspace(d).status() == 0
