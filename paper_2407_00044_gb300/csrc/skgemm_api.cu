@@ -1501,6 +1501,23 @@ struct FlipCopy {
   size_t offset;                // in the workspace, after the GEMM's own bytes
 };
 
+// Workspace bytes of the backward's GEMMs: the largest of the grouped plan
+// and, with two problems, each single-problem plan (the call runs one or
+// the other; the operand copies go after all of them).
+sk_status backward_gemm_ws(const sk_problem *pr, int n, const sk_config *cfg, size_t *bytes) {
+  size_t b = 0;
+  sk_status rc = sk_workspace_size(pr, n, cfg, &b);
+  if (rc != SK_OK) return rc;
+  for (int i = 0; n == 2 && i < n; ++i) {
+    size_t bi = 0;
+    rc = sk_workspace_size(&pr[i], 1, cfg, &bi);
+    if (rc != SK_OK) return rc;
+    b = std::max(b, bi);
+  }
+  *bytes = b;
+  return SK_OK;
+}
+
 // Plans the copies for problems pr[0..n) after `base` bytes of workspace;
 // returns the total workspace bytes the K-major path needs.
 size_t plan_flips(const sk_problem *pr, int n, size_t base, std::vector<FlipCopy> *out) {
@@ -1544,7 +1561,7 @@ sk_status sk_gemm_backward_workspace_size(const sk_problem *fwd, int need_dA, in
     return SK_OK;
   }
   size_t base = 0;
-  sk_status rc = sk_workspace_size(pr, n, cfg, &base);
+  sk_status rc = backward_gemm_ws(pr, n, cfg, &base);
   if (rc != SK_OK) return rc;
   std::vector<FlipCopy> flips;
   *bytes = plan_flips(pr, n, base, &flips);
@@ -1564,7 +1581,7 @@ sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc, 
   // operands are first copied to K-major layout there (one transpose
   // launch each), and the GEMMs read the copies.
   size_t base = 0;
-  if (ws && sk_workspace_size(pr, n, cfg, &base) == SK_OK) {
+  if (ws && backward_gemm_ws(pr, n, cfg, &base) == SK_OK) {
     std::vector<FlipCopy> flips;
     const size_t need = plan_flips(pr, n, base, &flips);
     bool degenerate = false;

@@ -596,3 +596,20 @@ def test_model_picks_wide_tile_for_long_k_dp(sk):
     assert g.tile_n != 512
     f = sk.plan(sk.shape_problem(8192, 8192, 8192, dtype="f32"), None, num_sms=152)
     assert f.tile_n != 512
+
+
+def test_backward_workspace_covers_single_launch_plans(sk):
+    """The operand copies sit after the largest GEMM workspace the backward
+    may use: the grouped plan or either single-problem plan (here 8192^3,
+    whose single plans take 256 x 512 tiles with 128 x 512 slots)."""
+    B = sk.binding
+    cfg = sk.Config(num_ctas=152).to_c()
+    fwd = sk.shape_problem(8192, 8192, 8192)
+    n = ctypes.c_size_t(0)
+    assert B.sk_gemm_backward_workspace_size(ctypes.byref(fwd), 1, 1, ctypes.byref(cfg), ctypes.byref(n)) == B.SK_OK
+    single = ctypes.c_size_t(0)
+    dA = sk.shape_problem(8192, 8192, 8192, b_layout="row")   # dA = dC B^T with B read MN-major
+    assert B.sk_workspace_size(ctypes.byref(dA), 1, ctypes.byref(cfg), ctypes.byref(single)) == B.SK_OK
+    assert single.value >= 152 * 128 * 512 * 4 // 2           # a 256 x 512 pair plan
+    copies = 3 * 8192 * 8192 * 2                               # B, A and dC
+    assert n.value >= single.value + copies
