@@ -7,6 +7,10 @@ copies every C back on a third, so problem i's GEMM overlaps problem i+1's
 upload and problem i-1's download.  Events order each problem's steps and
 keep a run from overwriting device buffers the previous run still uses.
 The GEMMs are ``api.gemm`` calls; this module only schedules copies.
+``run(join=False)`` leaves the current stream free, so consecutive runs
+overlap too (a run's uploads start as soon as the previous run's GEMM of
+the same problem has consumed its inputs); ``join()`` then makes the
+current stream wait for everything enqueued.
 """
 from __future__ import annotations
 
@@ -46,9 +50,10 @@ class HostGemmPipeline:
     def bytes_out(self) -> int:
         return sum(c.numel() * c.element_size() for _, _, c in self.host)
 
-    def run(self):
+    def run(self, join: bool = True):
         """Enqueue one pass over all problems after the current stream's
-        work; the current stream then waits for the last download."""
+        work; with ``join`` the current stream then waits for the last
+        download (else call ``join()`` after the last run)."""
         cur = torch.cuda.current_stream(self.device)
         for s in (self.h2d, self.comp, self.d2h):
             s.wait_stream(cur)
@@ -77,6 +82,13 @@ class HostGemmPipeline:
                 ev.record(self.d2h)
                 out_read.append(ev)
         self._done, self._out_read = done, out_read
+        if join:
+            self.join()
+
+    def join(self):
+        """The current stream waits for every upload, GEMM and download
+        enqueued so far."""
+        cur = torch.cuda.current_stream(self.device)
         cur.wait_stream(self.d2h)
         cur.wait_stream(self.h2d)
         cur.wait_stream(self.comp)
