@@ -128,9 +128,10 @@ struct OutStore<__nv_bfloat16> {
 // PAIR = false: one CTA per unit, 128 x BN tile, tcgen05 cta_group::1.
 // BN = 512 (pairs, BF16 / E4M3): two N = 256 MMAs per k-step into one
 //   512-column accumulator -- all of TMEM, so the epilogue of a tile is not
-//   overlapped by the next tile's MMAs -- with a quarter fewer shared-memory
-//   bytes (TMA writes + MMA operand reads) per MAC than a 256 x 256 pair.
-//   Each CTA holds B rows [r*128, r*128+128) of either MMA's 256 columns.
+//   overlapped by the next tile's MMAs -- loading a quarter fewer operand
+//   bytes per MAC than a 256 x 256 pair (12.5 % fewer shared-memory bytes,
+//   TMA writes plus MMA operand reads, as both MMAs read A).  Each CTA
+//   holds B rows [r*128, r*128+128) of either MMA's 256 columns.
 // PAIR = true : a cluster of two CTAs per unit, 256 x BN tile.  Each CTA
 //   TMA-loads its own 128 rows of A and its half (BN/2 rows) of B (either
 //   operand K-major or MN-major) into its
