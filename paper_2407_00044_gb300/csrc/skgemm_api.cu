@@ -1613,9 +1613,12 @@ sk_status sk_gemm_backward(const sk_problem *fwd, const void *dC, int64_t lddc, 
   // runtime model predicts faster; both write the same results' values up to
   // the summation order of each plan.
   if (n == 2) {
+    // (a configuration only single launches take -- 256 x 512 tiles --
+    // runs as two single launches too)
     sk_plan_info g, s0, s1;
-    if (sk_plan_query(pr, 2, cfg, 0, &g) == SK_OK && sk_plan_query(&pr[0], 1, cfg, 0, &s0) == SK_OK &&
-        sk_plan_query(&pr[1], 1, cfg, 0, &s1) == SK_OK && s0.predicted_us + s1.predicted_us < g.predicted_us) {
+    const bool grouped_ok = sk_plan_query(pr, 2, cfg, 0, &g) == SK_OK;
+    if (sk_plan_query(&pr[0], 1, cfg, 0, &s0) == SK_OK && sk_plan_query(&pr[1], 1, cfg, 0, &s1) == SK_OK &&
+        (!grouped_ok || s0.predicted_us + s1.predicted_us < g.predicted_us)) {
       sk_status rc = run(&pr[0], 1, cfg, ws, ws_bytes, st, 1);
       if (rc != SK_OK) return rc;
       return run(&pr[1], 1, cfg, ws, ws_bytes, st, 1);

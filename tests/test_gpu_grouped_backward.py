@@ -284,3 +284,16 @@ def test_transpose16_equals_torch(m, shape, ld_pad):
     y = m.transpose16(x)
     torch.cuda.synchronize()
     assert torch.equal(y.view(torch.int16), x.t().contiguous().view(torch.int16))
+
+
+def test_backward_with_wide_tile_config(m):
+    """An explicit 256 x 512 tile (single-problem launches only): the
+    backward runs its two GEMMs as single launches."""
+    M, N, K = 512, 1024, 768
+    d = dev()
+    a, b = workloads.gemm_inputs(M, N, K, dtype="bf16", seed=60)
+    g = workloads.normal((M, N), seed=61).to(torch.bfloat16)
+    dA, dB = m.gemm_backward(a.to(d), b.to(d), g.to(d), config=m.Config(tile_m=256, tile_n=512))
+    assert m.default_workspace(d).status() == 0
+    assert_within_bound(dA, g, b.t(), out="bf16", what="dA (256x512)")
+    assert_within_bound(dB, a.t(), g, out="bf16", what="dB (256x512)")
