@@ -1507,11 +1507,17 @@ struct FlipCopy {
 sk_status backward_gemm_ws(const sk_problem *pr, int n, const sk_config *cfg, size_t *bytes) {
   size_t b = 0;
   sk_status rc = sk_workspace_size(pr, n, cfg, &b);
-  if (rc != SK_OK) return rc;
-  for (int i = 0; n == 2 && i < n; ++i) {
+  if (n == 1) {
+    *bytes = b;
+    return rc;
+  }
+  // two problems: the grouped plan may be refused (a configuration only
+  // single launches take); the single plans must both resolve
+  if (rc != SK_OK) b = 0;
+  for (int i = 0; i < n; ++i) {
     size_t bi = 0;
-    rc = sk_workspace_size(&pr[i], 1, cfg, &bi);
-    if (rc != SK_OK) return rc;
+    const sk_status ri = sk_workspace_size(&pr[i], 1, cfg, &bi);
+    if (ri != SK_OK) return ri;
     b = std::max(b, bi);
   }
   *bytes = b;
