@@ -434,12 +434,14 @@ void build_plan(const std::vector<Norm> &probs, const std::vector<int> &idx, con
 // the previous tile's epilogue and for its last MMAs to drain.  A fit of
 // launch + items x (k-blocks x t_iter + t_item) to 14 DP shapes (K 1024 to
 // 16384, 1 to 27 tiles per pair) gave t_iter 560 ns, t_item 6.8 us and a
-// 7.9 us launch (2 % rms); the values below sit at the low edge of that fit
-// so that, against the 256 x 256 pair's coefficients, the model picks the
-// wide tile where it measured faster (8192^3, 8192 x 8192 x 16384,
-// 6144 x 6144 x 12288: 2-6 %) and not where it measured slower (K = 4096,
-// or more than ~10 tiles per pair).  Partials are twice a 256 x 256 pair's.
-#define PAIR512_COEFFS 550.0, 1500.0, 7920.0, 5000.0, 10060.0, 0.0, 6900.0, 8060.0
+// 7.9 us launch (2 % rms); against the 256 x 256 pair's coefficients the
+// values below pick the faster of the two tiles on all 21 shapes measured
+// both ways (the wide tile on 8192^3, 8192 x 8192 x {12288, 16384},
+// 6144 x 6144 x 12288, 16384 x 16384 x 8192 and 3072 x 3072 x 16384, by
+// 2-16 %; the pair on K = 4096 shapes, on 13.5 tiles per pair -- 8192 x
+// 16384 x 8192 both ways round -- and on short or small shapes).  Partials
+// are twice a 256 x 256 pair's.
+#define PAIR512_COEFFS 555.0, 1500.0, 7920.0, 5000.0, 10060.0, 0.0, 6900.0, 8060.0
 
 struct ModelCoeffs {
   double iter_ns;            // one k-block of one tile (effective; fitted with t_mac_item)

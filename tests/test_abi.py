@@ -586,10 +586,12 @@ def test_model_picks_wide_tile_for_long_k_dp(sk):
         i = sk.plan(sk.shape_problem(M, N, K), None, num_sms=152)
         return (i.tile_m, i.tile_n, i.mode)
     DP = sk.binding.SK_MODE_DP
-    for shape in [(8192, 8192, 8192), (8192, 8192, 16384), (6144, 6144, 12288)]:
+    for shape in [(8192, 8192, 8192), (8192, 8192, 16384), (6144, 6144, 12288), (8192, 8192, 12288),
+                  (16384, 16384, 8192), (3072, 3072, 16384)]:
         assert pick(*shape) == (256, 512, DP), shape
     for shape in [(8192, 8192, 4096), (4096, 14336, 4096), (16384, 16384, 4096), (3840, 4096, 4096),
-                  (2048, 7168, 1024), (1536, 1536, 8192)]:
+                  (2048, 7168, 1024), (1536, 1536, 8192), (8192, 16384, 8192), (16384, 8192, 8192),
+                  (12288, 12288, 8192), (2048, 2048, 32768)]:
         assert pick(*shape)[1] != 512, shape
     # never for groups, FP32, or Stream-K / hybrid plans of the library's own
     g = sk.plan([sk.shape_problem(8192, 8192, 8192)] * 2, None, num_sms=152)
