@@ -1640,6 +1640,7 @@ sk_status sk_transpose16(const void *src, int64_t rows, int64_t cols, int64_t ld
   if (rows < 0 || cols < 0 || ((rows > 0 && cols > 0) && (!src || !dst))) return SK_ERR_INVALID_ARG;
   if (ld_src < cols || ld_dst < rows) return SK_ERR_INVALID_ARG;
   if ((reinterpret_cast<uintptr_t>(src) & 1u) || (reinterpret_cast<uintptr_t>(dst) & 1u)) return SK_ERR_INVALID_ARG;
+  if (rows == 0 || cols == 0) return SK_OK;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return fail_msg(SK_ERR_NO_DEVICE, "no CUDA device");

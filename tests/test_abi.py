@@ -615,3 +615,18 @@ def test_backward_workspace_covers_single_launch_plans(sk):
     assert single.value >= 152 * 128 * 512 * 4 // 2           # a 256 x 512 pair plan
     copies = 3 * 8192 * 8192 * 2                               # B, A and dC
     assert n.value >= single.value + copies
+
+
+def test_transpose16_argument_checks(sk):
+    """sk_transpose16 refuses bad arguments before touching a device, and an
+    empty matrix is nothing to do."""
+    B = sk.binding
+    L = B.load()
+    buf = (ctypes.c_uint16 * 64)()
+    p = ctypes.addressof(buf)
+    assert L.sk_transpose16(None, 4, 4, 4, None, 4, None) == B.SK_ERR_INVALID_ARG
+    assert L.sk_transpose16(p, 4, 8, 4, p, 4, None) == B.SK_ERR_INVALID_ARG       # ld_src < cols
+    assert L.sk_transpose16(p, 8, 4, 4, p, 4, None) == B.SK_ERR_INVALID_ARG       # ld_dst < rows
+    assert L.sk_transpose16(p + 1, 4, 4, 4, p, 4, None) == B.SK_ERR_INVALID_ARG   # odd address
+    assert L.sk_transpose16(p, -1, 4, 4, p, 4, None) == B.SK_ERR_INVALID_ARG
+    assert L.sk_transpose16(None, 0, 5, 5, None, 1, None) == B.SK_OK
